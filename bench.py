@@ -1,0 +1,296 @@
+"""Benchmark of the DMS hot path on GB300: grid vertices/s from a float32
+field to its D0/D2 persistence pairs.
+
+A step is one pass of the whole path over one field resident in HBM:
+dms_order -> dms_gradient -> dms_critical -> dms_diagram_d0d2.  The default
+workload is the 1024^3 field (sum of 256 Gaussians, sigma in [0.01, 0.1], plus
+U[0, 1e-2) noise), synthetic and seeded.  Every step re-reads inputs of 4 GiB
+and more, far larger than the 129 MB L2, so no flush is needed between steps.
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload
+on its own GPU (the path has no exchange step); the timed region is bracketed
+by barriers and the maximum time over ranks is used.
+
+--impl reference times the CPU oracle (the plain single-threaded restatement
+the tests check the GPU against) on bounded crops of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "c3": dict(desc="1024^3 float32, 256 Gaussians (sigma U[0.01,0.1], amplitude U[-1,1]) "
+                    "+ U[0,1e-2) noise", n=1024),
+    "c2": dict(desc="512^3 float32, U[0,1) quantised to 256 levels", n=512),
+    "c1": dict(desc="64^3 float32, 16 Gaussians (sigma U[0.05,0.2]) + U[0,1e-3) noise", n=64),
+}
+METRIC = "grid vertices/s to D0/D2 diagrams"
+
+
+def make_field(workload: str, n: int, device, seed=0):
+    from paper_2505_21266_gb300 import fields
+    if workload == "c3":
+        return fields.config3(seed, device, n=n)
+    if workload == "c2":
+        return fields.config2(seed, device, n=n)
+    return fields.config1(seed, device, n=n)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(field_np: np.ndarray, crop: int):
+    """The oracle, as it stands, on a crop of the workload (one host core)."""
+    import oracle
+    oracle.build()
+    sub = np.ascontiguousarray(field_np[:crop, :crop, :crop])
+    t0 = time.perf_counter()
+    oracle.run(sub)
+    dt = time.perf_counter() - t0
+    return {"value": sub.size / dt, "unit": "vertices/s", "cores": 1, "kind": "oracle",
+            "sample": f"full oracle path (order, gradient, critical, D0/D2) on a {crop}^3 crop "
+                      f"of the workload field, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """--impl reference: the oracle on bounded crops of the workload field."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import torch
+    import oracle
+    from paper_2505_21266_gb300 import fields
+    oracle.build()
+    wl = WORKLOADS[args.workload]
+    n = args.size or wl["n"]
+    crop = args.crop
+    # a crop of the same field, generated directly on the host
+    if args.workload == "c3":
+        full = fields.mixture_crop(n, crop, 256, (0.01, 0.1), 1e-2, 0).numpy()
+    elif args.workload == "c2":
+        full = fields.config2(0, n=crop).numpy()
+    else:
+        full = fields.mixture_crop(n, crop, 16, (0.05, 0.2), 1e-3, 0).numpy()
+    f = np.ascontiguousarray(full, dtype=np.float32)
+    for _ in range(args.warmup):
+        oracle.run(f)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.run(f)
+    dt = time.perf_counter() - t0
+    v = f.size * args.steps / dt
+    line = {"metric": METRIC, "value": v, "unit": "vertices/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": wl["desc"], "sample": f"{crop}^3 crop per step"},
+            "cpu_baseline": {"value": v, "unit": "vertices/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{crop}^3 crop of the workload per step"},
+            "e2e": {"value": v, "unit": "vertices/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
+    ap.add_argument("--size", type=int, default=0, help="override the grid edge length")
+    ap.add_argument("--crop", type=int, default=48, help="oracle crop edge (CPU legs)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+    import paper_2505_21266_gb300 as dms
+    from paper_2505_21266_gb300 import _lib
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lib = _lib.load()
+
+    wl = WORKLOADS[args.workload]
+    n = args.size or wl["n"]
+    f = make_field(args.workload, n, dev)
+    torch.cuda.synchronize()
+    nvert = f.numel()
+    stream = torch.cuda.current_stream(dev)
+
+    def step(field, ev=None):
+        st = torch.zeros(1, dtype=torch.int32, device=dev)
+        o = dms.order(field, status=st)
+        if ev is not None:
+            ev[0].record(stream)
+        g = dms.gradient(o)
+        if ev is not None:
+            ev[1].record(stream)
+        c = dms.critical(g)
+        d = dms.diagram_d0d2(field, o, g, c, status=st)
+        return d, st, c
+
+    for _ in range(args.warmup):
+        d, st, c = step(f)
+    torch.cuda.synchronize()
+    if int(st.item()) != 0:
+        raise RuntimeError(f"device status {int(st.item())}")
+    crit_counts = [int(x.numel()) for x in c]
+    n_pairs = [int(d.d0.shape[0]), int(d.d2.shape[0])]
+
+    if world > 1:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    torch.cuda.synchronize()
+    l0 = lib.dms_launch_count()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    t_start.record(stream)
+    for k in range(args.steps):
+        step(f, gev[k])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    launches = lib.dms_launch_count() - l0
+    clocks = sampler.stop()
+    ms = t_start.elapsed_time(t_end)
+    grad_ms = statistics.mean(a.elapsed_time(b) for a, b in gev)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    value = nvert * world * args.steps / (ms / 1e3)
+
+    # end to end through the public API, the field coming from pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        host = f.cpu().pin_memory()
+        h2d = host.numel() * 4
+        for _ in range(1):
+            dms.diagram_from_host(host, dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d2h = 0
+        for _ in range(args.steps):
+            d0, d2, ess = dms.diagram_from_host(host, dev)
+            d2h = d0.nbytes + d2.nbytes + ess.nbytes
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        e2e = {"value": nvert * world * args.steps / dt, "unit": "vertices/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    peak, peak_kind = load_peaks()
+    grad_bytes = nvert * (4 + 8 + 1)  # read order, write record and desc
+    achieved = grad_bytes / (grad_ms / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "vertices/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": wl["desc"], "n": n, "vertices": nvert,
+                   "l2": "inputs (4 GiB field, 4 GiB order) larger than L2, no flush",
+                   "critical": crit_counts, "pairs_d0_d2": n_pairs,
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "kernel": "gradient_kernel", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": peak_kind, "traffic": None,
+                     "kernel_ms": grad_ms, "algorithmic_bytes": grad_bytes},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "e2e": e2e,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(f.cpu().numpy(), args.crop)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

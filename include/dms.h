@@ -1,0 +1,187 @@
+/*
+ * dms.h -- C ABI of the GB300-native Discrete Morse Sandwich hot path.
+ *
+ * The method is the one of "Distributed Discrete Morse Sandwich" (arXiv
+ * 2505.21266): a scalar field on a 3D regular grid, triangulated by the
+ * Freudenthal (Kuhn) split, goes through
+ *   (i)   the global vertex order            (Sec. 2.1, Sec. 3 "Array Preconditioning"),
+ *   (ii)  Robins et al.'s lower-star discrete gradient (Sec. 2.3),
+ *   (iii) critical-simplex extraction         (Sec. 2.5 "zero-persistence skip", Sec. 3),
+ *   (iv)  the extremum-saddle pairs D0 and D2 (Sec. 2.5, Alg. 1 and its dual; Sec. 4).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Vertex v = x + nx*(y + ny*z), x fastest (Sec. 2.1, "vertex offsets in
+ *    memory").  Each dim must be >= 2 and nx*ny*nz < 2^32 - 1.
+ *  - Simplices are chains of cube corners (Kuhn split along the (1,1,1)
+ *    diagonal), anchored at their componentwise-smallest vertex a.  A cube
+ *    corner is a 3-bit mask (bit0 = +x, bit1 = +y, bit2 = +z).  Ids (int64):
+ *      vertex   v
+ *      edge     7a + k,  k -> corner {1,2,4,3,5,6,7}[k]          ({a, a+c})
+ *      triangle 12a + k, k -> (p,q) {(1,3),(2,3),(1,5),(4,5),(2,6),(4,6),
+ *                                   (1,7),(2,7),(4,7),(3,7),(5,7),(6,7)}[k]
+ *                                                              ({a, a+p, a+q})
+ *      tet      6a + k,  k -> (c1,c2) {(1,3),(1,5),(2,3),(2,6),(4,5),(4,6)}[k]
+ *                                                    ({a, a+c1, a+c2, a+7})
+ *    An id names a simplex only if all of its vertices are in the grid.
+ *  - Simplices are compared by the orders of their vertices listed by
+ *    decreasing value, lexicographically, a proper prefix first (Sec. 2.1).
+ *  - Every pointer argument is a DEVICE pointer owned by the caller unless
+ *    marked "host".  No entry point allocates memory.  Work is enqueued on
+ *    `stream` and is asynchronous unless stated otherwise.
+ *  - Return value: a dms_status for errors the host can see (NULL pointers,
+ *    bad dims, short workspace or capacity known on the host, CUDA launch
+ *    errors).  Errors that depend on the data (NaN input, capacity exceeded,
+ *    an iteration limit reached) are OR-ed as (1 << status) into the device
+ *    word *dstatus, which the caller zeroes beforehand and reads after a
+ *    synchronisation.
+ */
+#ifndef DMS_H_
+#define DMS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dms_dims {
+  int32_t nx, ny, nz; /* x fastest */
+} dms_dims;
+
+/* One persistence pair (Sec. 2.4): the pair is embedded at
+ * (f(birth simplex), f(death simplex)), f(s) being the highest vertex value
+ * of s; birth_vtx / death_vtx are those highest vertices.  D0: birth_id is a
+ * minimum (vertex id), death_id an edge id.  D2: birth_id is a triangle id,
+ * death_id a tetrahedron id.  The essential D0 class has death_id = -1,
+ * death = +inf, death_vtx = 0. */
+typedef struct dms_pair {
+  int64_t birth_id;
+  int64_t death_id;
+  float birth;
+  float death;
+  uint32_t birth_vtx;
+  uint32_t death_vtx;
+} dms_pair;
+
+typedef enum dms_status {
+  DMS_OK = 0,
+  DMS_ERR_NULL = 1,       /* a required pointer is NULL */
+  DMS_ERR_DIMS = 2,       /* a dim < 2, or nx*ny*nz >= 2^32 - 1 */
+  DMS_ERR_NAN = 3,        /* the field holds a NaN (device-detected) */
+  DMS_ERR_CAPACITY = 4,   /* an output list is too short; counts hold the need */
+  DMS_ERR_WORKSPACE = 5,  /* ws_bytes smaller than the *_workspace_size query */
+  DMS_ERR_CUDA = 6,       /* a CUDA call failed */
+  DMS_ERR_TIMEOUT = 7,    /* an iterative stage hit its iteration limit */
+  DMS_ERR_ARG = 8         /* another invalid argument */
+} dms_status;
+
+/* Human-readable text for a dms_status (static storage). */
+const char* dms_status_string(int status);
+
+/* Instrumentation, not part of the method: the number of CUDA kernels this
+ * library has launched since it was loaded (every entry point adds its own
+ * launches).  Not thread-safe; the benchmark reads it around its timed
+ * region. */
+int64_t dms_launch_count(void);
+
+/* Number of vertices of the grid, or 0 if the dims are invalid. */
+int64_t dms_num_vertices(dms_dims d);
+
+/* ------------------------------------------------------------------ (i) ---
+ * dms_order -- the global vertex order (Sec. 2.1; Sec. 3 "Array
+ * Preconditioning"): order[v] = position of v in the stable sort of the
+ * vertices by increasing f, -0.0 equal to +0.0, ties broken by the vertex
+ * offset v.  ±inf are ordinary values; a NaN anywhere sets (1 << DMS_ERR_NAN)
+ * in *dstatus (order is then unspecified).
+ *   f       [n] float32, read only.
+ *   order   [n] uint32 out (a permutation of 0..n-1).
+ *   ws      workspace of at least dms_order_workspace_size(d) bytes,
+ *           256-byte aligned, contents need not be initialised.
+ *   dstatus one int32 the caller zeroed.
+ */
+size_t dms_order_workspace_size(dms_dims d);
+int dms_order(const float* f, dms_dims d, uint32_t* order, void* ws, size_t ws_bytes,
+              int32_t* dstatus, void* stream);
+
+/* ----------------------------------------------------------------- (ii) ---
+ * dms_gradient -- Robins et al.'s discrete gradient, computed vertex by vertex
+ * on its lower star (Sec. 2.3): ProcessLowerStars with priority queues on
+ * the lexicographic key, the steepest lower edge paired with the vertex.
+ *   order   [n] uint32 from dms_order (any permutation works: it IS the order).
+ *   desc    [n] uint8 out.  desc[v] = 0..13: v is paired with its edge to the
+ *           neighbour v + off[desc] where off[s] is +c for s < 7 and -c for
+ *           s >= 7, c = corner {1,2,4,3,5,6,7}[s % 7]; 15: v is critical (a
+ *           minimum).
+ *   rec     [n] uint64 out, one record per anchor a, describing the 7 edges,
+ *           12 triangles and 6 tetrahedra anchored at a:
+ *             bits 3k..3k+2 (edge k):  0 = absent or paired with its top
+ *                vertex, 1..6 = paired with the (code-1)-th triangle holding
+ *                it, cofacets listed by increasing id on the unbounded
+ *                lattice, 7 = critical;
+ *             bit 21+k (triangle k): 1 = critical;
+ *             bits 33+3k..35+3k (tet k): 0 = absent, 1..4 = paired with the
+ *                facet that omits vertex (code-1) of the chain
+ *                a < a+c1 < a+c2 < a+7, 7 = critical;
+ *             other bits 0.
+ *           Triangles paired with an edge are recorded at that edge, those
+ *           paired with a tetrahedron at the tetrahedron.
+ *   crit_counts [4] int64 out: number of critical simplices per dimension
+ *           (overwritten, not accumulated).
+ */
+int dms_gradient(const uint32_t* order, dms_dims d, uint8_t* desc, uint64_t* rec,
+                 int64_t* crit_counts, void* stream);
+
+/* ---------------------------------------------------------------- (iii) ---
+ * dms_critical -- stream compaction of the critical simplices ("zero-
+ * persistence skip", Sec. 2.5; "Extract & sort", Sec. 3): crit_k receives the
+ * ids of the critical k-simplices in increasing id order.
+ *   desc, rec  from dms_gradient.
+ *   crit0..3   int64 out arrays of capacity cap[k] (host array of 4).
+ *   counts     [4] int64 out: the number of critical k-simplices.  If one
+ *              exceeds cap[k], (1 << DMS_ERR_CAPACITY) is set in *dstatus and
+ *              only the first cap[k] ids are written.
+ *   ws         at least dms_critical_workspace_size(d) bytes.
+ */
+size_t dms_critical_workspace_size(dms_dims d);
+int dms_critical(const uint8_t* desc, const uint64_t* rec, dms_dims d, int64_t* crit0,
+                 int64_t* crit1, int64_t* crit2, int64_t* crit3, const int64_t* cap,
+                 int64_t* counts, void* ws, size_t ws_bytes, int32_t* dstatus, void* stream);
+
+/* ----------------------------------------------------------------- (iv) ---
+ * dms_diagram_d0d2 -- the extremum-saddle persistence pairs (Sec. 2.5, Alg. 1,
+ * Sec. 4.1-4.2).  D0: from both vertices of every critical edge the
+ * descending v-path is followed to a minimum; the triplets (edge, t0, t1)
+ * with t0 != t1 are taken in increasing edge order and, with a union-find
+ * over minima, the younger (higher) root dies against the edge.  D2: from the
+ * two cofacets of every critical triangle the dual (ascending) v-path is
+ * followed to a critical tetrahedron, or to a virtual OUTSIDE node when the
+ * path leaves the grid; triangles are taken in decreasing order and the lower
+ * maximum dies (OUTSIDE never dies).  The pairing rounds are exact: each
+ * round merges the saddles that are the lightest live saddle of both of
+ * their components, which is the order Alg. 1 would have used on them.
+ *   f, order, desc, rec   as above;  crit0..3 and n_crit (HOST array of 4)
+ *                         from dms_critical.
+ *   d0   [cap0] out: D0 pairs in increasing edge order (n_crit[0]-1 of them
+ *        for a grid, plus the essential class written to *d0_essential).
+ *   d2   [cap2] out: D2 pairs in decreasing triangle order (n_crit[3]).
+ *   n_out [2] int64 out: numbers of D0 and D2 pairs (capacity errors as in
+ *        dms_critical).
+ *   ws   at least dms_diagram_workspace_size(d, n_crit) bytes.
+ * This call synchronises `stream` between pairing rounds (it reads the
+ * number of live saddles on the host).
+ */
+size_t dms_diagram_workspace_size(dms_dims d, const int64_t* n_crit);
+int dms_diagram_d0d2(const float* f, const uint32_t* order, const uint8_t* desc,
+                     const uint64_t* rec, dms_dims d, const int64_t* crit0,
+                     const int64_t* crit1, const int64_t* crit2, const int64_t* crit3,
+                     const int64_t* n_crit, dms_pair* d0, int64_t cap0, dms_pair* d2,
+                     int64_t cap2, dms_pair* d0_essential, int64_t* n_out, void* ws,
+                     size_t ws_bytes, int32_t* dstatus, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DMS_H_ */

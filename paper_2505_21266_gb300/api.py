@@ -1,0 +1,199 @@
+"""Python front end of the DMS hot path: argument marshalling around the C ABI.
+
+Tensors are torch CUDA tensors (PyTorch provides device memory and streams);
+every computation runs in ``libdms_gb300.so``.  Fields are indexed
+``field[z, y, x]`` (x fastest, the vertex offset v = x + nx*(y + ny*z)).
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib
+
+PAIR_DTYPE = np.dtype([("birth_id", "<i8"), ("death_id", "<i8"), ("birth", "<f4"),
+                       ("death", "<f4"), ("birth_vtx", "<u4"), ("death_vtx", "<u4")])
+PAIR_BYTES = 32
+CRITICAL = 7  # record code of a critical edge / tetrahedron
+
+
+class DMSError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = int(code)
+        super().__init__(f"{where}: {_lib.status_name(code)}")
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise DMSError(rc, where)
+
+
+def _device_status_check(st: torch.Tensor, where: str):
+    v = int(st.item())
+    if v:
+        codes = [c for c in range(1, 9) if v & (1 << c)]
+        raise DMSError(codes[0], where)
+
+
+def dims_of(field: torch.Tensor) -> _lib.dms_dims:
+    if field.dim() != 3:
+        raise ValueError("field must be a 3D tensor indexed [z, y, x]")
+    nz, ny, nx = field.shape
+    return _lib.dms_dims(nx, ny, nz)
+
+
+def _require_cuda(t: torch.Tensor, name: str, dtype=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (the DMS library has no CPU path)")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def _stream(device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _ws(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+# ------------------------------------------------------------------- (i) --
+
+def order(field: torch.Tensor, status: torch.Tensor | None = None, check: bool = True):
+    """Global vertex order (Sec. 2.1, Sec. 3): uint32 tensor shaped like field."""
+    _require_cuda(field, "field", torch.float32)
+    lib = _lib.load()
+    d = dims_of(field)
+    out = torch.empty(field.shape, dtype=torch.uint32, device=field.device)
+    ws = _ws(lib.dms_order_workspace_size(d), field.device)
+    st = status if status is not None else torch.zeros(1, dtype=torch.int32, device=field.device)
+    _check(lib.dms_order(_ptr(field), d, _ptr(out), _ptr(ws), ws.numel(), _ptr(st),
+                         _stream(field.device)), "dms_order")
+    if check and status is None:
+        _device_status_check(st, "dms_order")
+    return out
+
+
+# ------------------------------------------------------------------ (ii) --
+
+@dataclass
+class Gradient:
+    desc: torch.Tensor    # uint8 [nz, ny, nx]
+    rec: torch.Tensor     # int64 [nz, ny, nx] (bit pattern of the uint64 records)
+    counts: torch.Tensor  # int64 [4] critical simplices per dimension
+
+
+def gradient(order_t: torch.Tensor) -> Gradient:
+    """Robins et al.'s lower-star discrete gradient (Sec. 2.3)."""
+    _require_cuda(order_t, "order", torch.uint32)
+    lib = _lib.load()
+    d = dims_of(order_t)
+    desc = torch.empty(order_t.shape, dtype=torch.uint8, device=order_t.device)
+    rec = torch.empty(order_t.shape, dtype=torch.int64, device=order_t.device)
+    counts = torch.empty(4, dtype=torch.int64, device=order_t.device)
+    _check(lib.dms_gradient(_ptr(order_t), d, _ptr(desc), _ptr(rec), _ptr(counts),
+                            _stream(order_t.device)), "dms_gradient")
+    return Gradient(desc, rec, counts)
+
+
+# ----------------------------------------------------------------- (iii) --
+
+def critical(g: Gradient, caps=None, status: torch.Tensor | None = None):
+    """Critical simplices per dimension, each list sorted by id (int64).
+    Without ``caps`` the capacities are read from ``g.counts`` (one sync)."""
+    lib = _lib.load()
+    dev = g.desc.device
+    d = dims_of(g.desc)
+    if caps is None:
+        caps = [int(x) for x in g.counts.cpu()]
+    lists = [torch.empty(max(int(c), 1), dtype=torch.int64, device=dev) for c in caps]
+    cap_arr = (ctypes.c_int64 * 4)(*[int(c) for c in caps])
+    counts = torch.empty(4, dtype=torch.int64, device=dev)
+    ws = _ws(lib.dms_critical_workspace_size(d), dev)
+    st = status if status is not None else torch.zeros(1, dtype=torch.int32, device=dev)
+    _check(lib.dms_critical(_ptr(g.desc), _ptr(g.rec), d, *[_ptr(t) for t in lists], cap_arr,
+                            _ptr(counts), _ptr(ws), ws.numel(), _ptr(st), _stream(dev)),
+           "dms_critical")
+    if status is None:
+        _device_status_check(st, "dms_critical")
+        n = [int(x) for x in counts.cpu()]
+        return [lists[k][: n[k]] for k in range(4)]
+    return lists, counts
+
+
+# ------------------------------------------------------------------ (iv) --
+
+@dataclass
+class Diagrams:
+    d0: torch.Tensor           # uint8 [n0, 32] pair records (see PAIR_DTYPE)
+    d2: torch.Tensor           # uint8 [n2, 32]
+    d0_essential: torch.Tensor  # uint8 [1, 32]
+
+    def numpy(self, which: str) -> np.ndarray:
+        t = getattr(self, which)
+        return t.cpu().numpy().view(PAIR_DTYPE).reshape(-1)
+
+
+def diagram_d0d2(field: torch.Tensor, order_t: torch.Tensor, g: Gradient, crit,
+                 status: torch.Tensor | None = None) -> Diagrams:
+    """D0 and D2 pairs (Sec. 2.5, Alg. 1 and its dual; Sec. 4)."""
+    _require_cuda(field, "field", torch.float32)
+    lib = _lib.load()
+    dev = field.device
+    d = dims_of(field)
+    nc = [int(c.numel()) for c in crit]
+    ncarr = (ctypes.c_int64 * 4)(*nc)
+    cap0, cap2 = max(nc[0] - 1, 0), nc[3]
+    d0 = torch.empty((max(cap0, 1), PAIR_BYTES), dtype=torch.uint8, device=dev)
+    d2 = torch.empty((max(cap2, 1), PAIR_BYTES), dtype=torch.uint8, device=dev)
+    ess = torch.zeros((1, PAIR_BYTES), dtype=torch.uint8, device=dev)
+    n_out = torch.zeros(2, dtype=torch.int64, device=dev)
+    ws = _ws(lib.dms_diagram_workspace_size(d, ncarr), dev)
+    st = status if status is not None else torch.zeros(1, dtype=torch.int32, device=dev)
+    crit_p = [_ptr(c) if c.numel() else None for c in crit]
+    _check(lib.dms_diagram_d0d2(_ptr(field), _ptr(order_t), _ptr(g.desc), _ptr(g.rec), d,
+                                *crit_p, ncarr, _ptr(d0), cap0, _ptr(d2), cap2, _ptr(ess),
+                                _ptr(n_out), _ptr(ws), ws.numel(), _ptr(st), _stream(dev)),
+           "dms_diagram_d0d2")
+    if status is None:
+        _device_status_check(st, "dms_diagram_d0d2")
+    n = [int(x) for x in n_out.cpu()]
+    return Diagrams(d0[: n[0]], d2[: n[1]], ess)
+
+
+@dataclass
+class Result:
+    order: torch.Tensor
+    grad: Gradient
+    crit: list
+    diagrams: Diagrams
+
+
+def diagram(field: torch.Tensor) -> Result:
+    """The whole hot path: order -> gradient -> critical simplices -> D0/D2."""
+    o = order(field)
+    g = gradient(o)
+    c = critical(g)
+    dg = diagram_d0d2(field, o, g, c)
+    return Result(o, g, c, dg)
+
+
+def diagram_from_host(field_host, device="cuda"):
+    """End-to-end call for data that lives in host memory: copies the field to
+    the device, runs the whole path, and returns the D0 / D2 pairs and the
+    essential class as numpy structured arrays (PAIR_DTYPE)."""
+    if not isinstance(field_host, torch.Tensor):
+        field_host = torch.from_numpy(np.ascontiguousarray(field_host, dtype=np.float32))
+    f = field_host.to(device, non_blocking=True)
+    res = diagram(f)
+    return (res.diagrams.numpy("d0"), res.diagrams.numpy("d2"),
+            res.diagrams.numpy("d0_essential"))

@@ -1,0 +1,127 @@
+// C ABI entry points (include/dms.h): argument validation, workspace checks
+// and the launches.  Nothing here allocates memory.
+#include <cstdint>
+
+#include "dms_common.cuh"
+
+namespace dms {
+int launch_order(const float* f, const Grid& g, uint32_t* order, void* ws, int32_t* dstatus,
+                 cudaStream_t s);
+size_t order_workspace_bytes(const Grid& g);
+int launch_gradient(const uint32_t* order, const Grid& g, uint8_t* desc, uint64_t* rec,
+                    int64_t* crit_counts, cudaStream_t s);
+size_t critical_workspace_bytes(const Grid& g);
+int launch_critical(const uint8_t* desc, const uint64_t* rec, const Grid& g, int64_t* c0,
+                    int64_t* c1, int64_t* c2, int64_t* c3, const int64_t cap[4], int64_t* counts,
+                    void* ws, int32_t* dstatus, cudaStream_t s);
+size_t diagram_workspace_bytes(const Grid& g, const int64_t* n_crit);
+int launch_diagram(const float* f, const uint32_t* order, const uint8_t* desc, const uint64_t* rec,
+                   const Grid& g, const int64_t* crit0, const int64_t* crit1, const int64_t* crit2,
+                   const int64_t* crit3, const int64_t* nc, dms_pair* d0, int64_t cap0,
+                   dms_pair* d2, int64_t cap2, dms_pair* ess, int64_t* n_out, void* ws,
+                   int32_t* dstatus, cudaStream_t s);
+long long& launch_counter() {
+  static long long n = 0;
+  return n;
+}
+}  // namespace dms
+
+using dms::Grid;
+
+extern "C" {
+
+const char* dms_status_string(int status) {
+  switch (status) {
+    case DMS_OK: return "ok";
+    case DMS_ERR_NULL: return "a required pointer is NULL";
+    case DMS_ERR_DIMS: return "invalid dims (each >= 2, fewer than 2^32 - 1 vertices)";
+    case DMS_ERR_NAN: return "the field holds a NaN";
+    case DMS_ERR_CAPACITY: return "an output list is too short";
+    case DMS_ERR_WORKSPACE: return "workspace too small";
+    case DMS_ERR_CUDA: return "a CUDA call failed";
+    case DMS_ERR_TIMEOUT: return "an iterative stage hit its iteration limit";
+    case DMS_ERR_ARG: return "invalid argument";
+  }
+  return "unknown status";
+}
+
+int64_t dms_launch_count(void) { return dms::launch_counter(); }
+
+int64_t dms_num_vertices(dms_dims d) {
+  Grid g;
+  return dms::make_grid(d, &g) ? g.n : 0;
+}
+
+size_t dms_order_workspace_size(dms_dims d) {
+  Grid g;
+  return dms::make_grid(d, &g) ? dms::order_workspace_bytes(g) : 0;
+}
+
+int dms_order(const float* f, dms_dims d, uint32_t* order, void* ws, size_t ws_bytes,
+              int32_t* dstatus, void* stream) {
+  Grid g;
+  if (!dms::make_grid(d, &g)) return DMS_ERR_DIMS;
+  if (!f || !order || !ws || !dstatus) return DMS_ERR_NULL;
+  if (ws_bytes < dms::order_workspace_bytes(g)) return DMS_ERR_WORKSPACE;
+  return dms::launch_order(f, g, order, ws, dstatus, static_cast<cudaStream_t>(stream));
+}
+
+int dms_gradient(const uint32_t* order, dms_dims d, uint8_t* desc, uint64_t* rec,
+                 int64_t* crit_counts, void* stream) {
+  Grid g;
+  if (!dms::make_grid(d, &g)) return DMS_ERR_DIMS;
+  if (!order || !desc || !rec || !crit_counts) return DMS_ERR_NULL;
+  return dms::launch_gradient(order, g, desc, rec, crit_counts, static_cast<cudaStream_t>(stream));
+}
+
+size_t dms_critical_workspace_size(dms_dims d) {
+  Grid g;
+  return dms::make_grid(d, &g) ? dms::critical_workspace_bytes(g) : 0;
+}
+
+int dms_critical(const uint8_t* desc, const uint64_t* rec, dms_dims d, int64_t* crit0,
+                 int64_t* crit1, int64_t* crit2, int64_t* crit3, const int64_t* cap,
+                 int64_t* counts, void* ws, size_t ws_bytes, int32_t* dstatus, void* stream) {
+  Grid g;
+  if (!dms::make_grid(d, &g)) return DMS_ERR_DIMS;
+  if (!desc || !rec || !cap || !counts || !ws || !dstatus) return DMS_ERR_NULL;
+  int64_t* lists[4] = {crit0, crit1, crit2, crit3};
+  for (int k = 0; k < 4; ++k) {
+    if (cap[k] < 0) return DMS_ERR_ARG;
+    if (cap[k] > 0 && !lists[k]) return DMS_ERR_NULL;
+  }
+  if (ws_bytes < dms::critical_workspace_bytes(g)) return DMS_ERR_WORKSPACE;
+  return dms::launch_critical(desc, rec, g, crit0, crit1, crit2, crit3, cap, counts, ws, dstatus,
+                              static_cast<cudaStream_t>(stream));
+}
+
+size_t dms_diagram_workspace_size(dms_dims d, const int64_t* n_crit) {
+  Grid g;
+  if (!dms::make_grid(d, &g) || !n_crit) return 0;
+  return dms::diagram_workspace_bytes(g, n_crit);
+}
+
+int dms_diagram_d0d2(const float* f, const uint32_t* order, const uint8_t* desc,
+                     const uint64_t* rec, dms_dims d, const int64_t* crit0,
+                     const int64_t* crit1, const int64_t* crit2, const int64_t* crit3,
+                     const int64_t* n_crit, dms_pair* d0, int64_t cap0, dms_pair* d2,
+                     int64_t cap2, dms_pair* d0_essential, int64_t* n_out, void* ws,
+                     size_t ws_bytes, int32_t* dstatus, void* stream) {
+  Grid g;
+  if (!dms::make_grid(d, &g)) return DMS_ERR_DIMS;
+  if (!f || !order || !desc || !rec || !n_crit || !d0_essential || !n_out || !ws || !dstatus)
+    return DMS_ERR_NULL;
+  const int64_t* lists[4] = {crit0, crit1, crit2, crit3};
+  for (int k = 0; k < 4; ++k) {
+    if (n_crit[k] < 0 || n_crit[k] >= 0xFFFFFFFFll) return DMS_ERR_ARG;
+    if (n_crit[k] > 0 && !lists[k]) return DMS_ERR_NULL;
+  }
+  if (n_crit[0] < 1) return DMS_ERR_ARG;  // a grid always has a minimum
+  if (cap0 < 0 || cap2 < 0 || (cap0 > 0 && !d0) || (cap2 > 0 && !d2)) return DMS_ERR_ARG;
+  if (ws_bytes < dms::diagram_workspace_bytes(g, n_crit)) return DMS_ERR_WORKSPACE;
+  return dms::launch_diagram(f, order, desc, rec, g, crit0, crit1, crit2, crit3, n_crit, d0, cap0,
+                             d2, cap2, d0_essential, n_out, ws, dstatus,
+                             static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,156 @@
+// Critical-simplex extraction ("zero-persistence skip", Sec. 2.5; "Extract &
+// sort", Sec. 3): ordered stream compaction of the simplices the gradient left
+// unpaired.  The records are anchor-indexed, so a compaction in anchor order
+// (then type order inside an anchor) yields every list sorted by id with no
+// sort at all.  Two passes over the records: per-tile counts, a device-wide
+// scan, then per-tile writes with block-level scans for the offsets.
+#include <cstdint>
+
+#include "dms_common.cuh"
+#include "dms_scan.cuh"
+
+namespace dms {
+namespace {
+
+constexpr int CNT = 256;
+constexpr int CITEMS = 16;
+constexpr int CTILE = CNT * CITEMS;
+
+constexpr uint64_t kEdgeLsb = 0x49249ull;
+constexpr uint64_t kTriMask = 0xFFFull << 21;
+constexpr uint64_t kTetLsb = 0x9249ull << 33;
+
+__device__ __forceinline__ void anchor_counts(uint8_t d, uint64_t r, int c[4]) {
+  c[0] = d == 15;
+  c[1] = __popcll(r & (r >> 1) & (r >> 2) & kEdgeLsb);
+  c[2] = __popcll(r & kTriMask);
+  c[3] = __popcll(r & (r >> 1) & (r >> 2) & kTetLsb);
+}
+
+struct TileSmem {
+  unsigned long long rec[CTILE];
+  uint8_t desc[CTILE];
+  long long tmp[32];
+};
+
+__device__ __forceinline__ void stage(TileSmem& sm, const uint8_t* desc, const uint64_t* rec,
+                                      int64_t a0, int64_t n) {
+  for (int i = threadIdx.x; i < CTILE; i += CNT) {
+    int64_t a = a0 + i;
+    sm.rec[i] = a < n ? __ldg(reinterpret_cast<const unsigned long long*>(rec) + a) : 0ull;
+    sm.desc[i] = a < n ? __ldg(desc + a) : (uint8_t)0;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(CNT) count_kernel(const uint8_t* __restrict__ desc,
+                                                    const uint64_t* __restrict__ rec, int64_t n,
+                                                    int64_t ntiles, long long* __restrict__ bc) {
+  __shared__ TileSmem sm;
+  const int64_t a0 = (int64_t)blockIdx.x * CTILE;
+  stage(sm, desc, rec, a0, n);
+  int tot[4] = {0, 0, 0, 0};
+  for (int k = 0; k < CITEMS; ++k) {
+    int i = threadIdx.x * CITEMS + k;
+    int c[4];
+    anchor_counts(sm.desc[i], sm.rec[i], c);
+    if (a0 + i >= n) c[0] = 0;
+    for (int d = 0; d < 4; ++d) tot[d] += c[d];
+  }
+  for (int d = 0; d < 4; ++d) {
+    long long t;
+    scan64::block_excl(tot[d], sm.tmp, &t);
+    if (threadIdx.x == 0) bc[d * ntiles + blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(CNT) write_kernel(const uint8_t* __restrict__ desc,
+                                                    const uint64_t* __restrict__ rec, int64_t n,
+                                                    int64_t ntiles,
+                                                    const long long* __restrict__ boff,
+                                                    int64_t* c0, int64_t* c1, int64_t* c2,
+                                                    int64_t* c3, int64_t cap0, int64_t cap1,
+                                                    int64_t cap2, int64_t cap3) {
+  __shared__ TileSmem sm;
+  const int64_t a0 = (int64_t)blockIdx.x * CTILE;
+  stage(sm, desc, rec, a0, n);
+  int tot[4] = {0, 0, 0, 0};
+  for (int k = 0; k < CITEMS; ++k) {
+    int i = threadIdx.x * CITEMS + k;
+    int c[4];
+    anchor_counts(sm.desc[i], sm.rec[i], c);
+    if (a0 + i >= n) c[0] = 0;
+    for (int d = 0; d < 4; ++d) tot[d] += c[d];
+  }
+  long long off[4];
+  for (int d = 0; d < 4; ++d) {
+    long long e = scan64::block_excl(tot[d], sm.tmp, nullptr);
+    off[d] = e + (boff[d * ntiles + blockIdx.x] - boff[d * ntiles]);
+  }
+  for (int k = 0; k < CITEMS; ++k) {
+    int i = threadIdx.x * CITEMS + k;
+    int64_t a = a0 + i;
+    if (a >= n) break;
+    uint64_t r = sm.rec[i];
+    if (sm.desc[i] == 15) {
+      if (off[0] < cap0) c0[off[0]] = a;
+      ++off[0];
+    }
+    if (!r) continue;
+    for (int t = 0; t < 7; ++t)
+      if (((r >> (3 * t)) & 7ull) == 7ull) {
+        if (off[1] < cap1) c1[off[1]] = 7 * a + t;
+        ++off[1];
+      }
+    for (int t = 0; t < 12; ++t)
+      if ((r >> (21 + t)) & 1ull) {
+        if (off[2] < cap2) c2[off[2]] = 12 * a + t;
+        ++off[2];
+      }
+    for (int t = 0; t < 6; ++t)
+      if (((r >> (33 + 3 * t)) & 7ull) == 7ull) {
+        if (off[3] < cap3) c3[off[3]] = 6 * a + t;
+        ++off[3];
+      }
+  }
+}
+
+__global__ void finish_kernel(const long long* __restrict__ boff, const long long* __restrict__ total,
+                              int64_t ntiles, int64_t* counts, int64_t cap0, int64_t cap1,
+                              int64_t cap2, int64_t cap3, int32_t* dstatus) {
+  if (threadIdx.x != 0) return;
+  const int64_t caps[4] = {cap0, cap1, cap2, cap3};
+  for (int d = 0; d < 4; ++d) {
+    long long lo = boff[d * ntiles];
+    long long hi = d < 3 ? boff[(d + 1) * ntiles] : *total;
+    counts[d] = hi - lo;
+    if (hi - lo > caps[d]) set_status(dstatus, DMS_ERR_CAPACITY);
+  }
+}
+
+}  // namespace
+
+size_t critical_workspace_bytes(const Grid& g) {
+  const int64_t ntiles = (g.n + CTILE - 1) / CTILE;
+  const int64_t m = 4 * ntiles;
+  return align_up(m * sizeof(long long)) + align_up((scan64::num_sums(m) + 1) * sizeof(long long));
+}
+
+int launch_critical(const uint8_t* desc, const uint64_t* rec, const Grid& g, int64_t* c0,
+                    int64_t* c1, int64_t* c2, int64_t* c3, const int64_t cap[4], int64_t* counts,
+                    void* ws, int32_t* dstatus, cudaStream_t s) {
+  const int64_t ntiles = (g.n + CTILE - 1) / CTILE;
+  const int64_t m = 4 * ntiles;
+  WsCarver c(ws);
+  long long* bc = c.take<long long>(m);
+  long long* sums = c.take<long long>(scan64::num_sums(m) + 1);
+  count_kernel<<<(unsigned)ntiles, CNT, 0, s>>>(desc, rec, g.n, ntiles, bc); count_launch();
+  scan64::run(bc, m, sums, s);
+  write_kernel<<<(unsigned)ntiles, CNT, 0, s>>>(desc, rec, g.n, ntiles, bc, c0, c1, c2, c3, cap[0],
+                                                cap[1], cap[2], cap[3]); count_launch();
+  finish_kernel<<<1, 32, 0, s>>>(bc, sums + scan64::num_sums(m), ntiles, counts, cap[0], cap[1],
+                                 cap[2], cap[3], dstatus); count_launch();
+  return launch_status();
+}
+
+}  // namespace dms

@@ -1,0 +1,194 @@
+// Robins et al.'s lower-star discrete gradient (Sec. 2.3) on the Freudenthal
+// triangulation of a 3D grid -- the first and most time-consuming step of DMS.
+//
+// One thread runs ProcessLowerStars for one vertex x.  The lower star L(x) --
+// the simplices holding x whose other vertices all precede x -- lives in
+// bitmasks over the fixed star numbering (14 edges, 36 triangles, 24 tets).
+// The two priority queues of the algorithm (PQzero, PQone) are bitmask sets
+// whose pop-min compares 12-bit keys: the ranks, among the lower neighbours
+// of x, of a simplex's other vertices listed by decreasing order (for
+// simplices that all hold x this is the lexicographic comparison of Sec. 2.1,
+// a proper prefix first).
+//
+// Work layout: a CTA owns a TX x TY x ZC block of ANCHORS and streams it
+// along z.  Every simplex is recorded at its anchor but decided in the lower
+// star of its highest vertex, which lies in anchor + {0,1}^3; the CTA therefore
+// processes the vertices of its block plus a one-vertex halo on the +x, +y and
+// +z sides (6% extra work at 32 x 32) and assembles whole records in shared
+// memory with shared atomics -- no global atomics, no memset, coalesced
+// stores.  The order field is staged slab by slab in a 3-slab ring of
+// (TX+3) x (TY+3) windows (out-of-grid vertices read as 0xFFFFFFFF, i.e.
+// never lower).
+#include <algorithm>
+#include <cstdint>
+#include <type_traits>
+
+#include "dms_common.cuh"
+#include "dms_lowerstar.cuh"
+#include "dms_star.cuh"
+
+namespace dms {
+namespace {
+
+constexpr int TX = 32, TY = 32;
+constexpr int WX = TX + 3, WY = TY + 3;
+constexpr int NT = 256;
+constexpr int NKEYS = 14 + 36 + 24;
+
+__constant__ StarTables cStar = kStar;
+
+using lowerstar::static_for;
+
+constexpr uint64_t kEdgeLsb = 0x49249ull;      // bits 0,3,..,18
+constexpr uint64_t kTriMask = 0xFFFull << 21;  // bits 21..32
+constexpr uint64_t kTetLsb = 0x9249ull << 33;  // bits 33,36,..,48
+
+struct Smem {
+  lowerstar::Tables tb;
+  uint32_t win[3][WY][WX];
+  unsigned long long recs[2][TY][TX];
+  uint16_t keys[NKEYS][NT];
+  unsigned int counts[4];
+};
+
+__device__ __forceinline__ void load_slab(Smem& sm, const uint32_t* __restrict__ order,
+                                          const Grid& g, int x0, int y0, int64_t zs, int slot) {
+  for (int i = threadIdx.x; i < WX * WY; i += NT) {
+    int wx = i % WX, wy = i / WX;
+    int64_t gx = x0 - 1 + wx, gy = y0 - 1 + wy;
+    uint32_t v = 0xFFFFFFFFu;
+    if (zs >= 0 && zs < g.nz && gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny)
+      v = __ldg(order + gx + g.nx * (gy + g.ny * zs));
+    sm.win[slot][wy][wx] = v;
+  }
+}
+
+__global__ void __launch_bounds__(NT) gradient_kernel(const uint32_t* __restrict__ order, Grid g,
+                                                      int zc, uint8_t* __restrict__ desc,
+                                                      uint64_t* __restrict__ rec,
+                                                      unsigned long long* __restrict__ counts) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int64_t z0 = (int64_t)blockIdx.z * zc;
+  const int64_t zend = (z0 + zc < g.nz) ? z0 + zc : g.nz;     // anchor slabs [z0, zend)
+  const int64_t zlast = (zend < g.nz - 1) ? zend : g.nz - 1;   // vertex slabs [z0, zlast]
+
+  // tables into shared memory (dynamic indexing)
+  for (int i = tid; i < 36; i += NT) {
+    sm.tb.triCof[i] = cStar.triCof[i];
+    sm.tb.triEdges[i] = (uint16_t)cStar.triEdges[i];
+    sm.tb.triA[i] = (uint8_t)cStar.triA[i];
+    sm.tb.triB[i] = (uint8_t)cStar.triB[i];
+    sm.tb.cofIdx[i][0] = (uint8_t)cStar.cofIdx[i][0];
+    sm.tb.cofIdx[i][1] = (uint8_t)cStar.cofIdx[i][1];
+  }
+  for (int i = tid; i < 24; i += NT) {
+    sm.tb.tetFmask[i] = cStar.tetFmask[i];
+    for (int w = 0; w < 3; ++w) sm.tb.tetF[i][w] = (uint8_t)cStar.tetF[i][w];
+  }
+  for (int i = tid; i < 14; i += NT) sm.tb.edgeCof[i] = cStar.edgeCof[i];
+  for (int i = tid; i < 2 * TX * TY; i += NT) (&sm.recs[0][0][0])[i] = 0ull;
+  if (tid < 4) sm.counts[tid] = 0;
+  load_slab(sm, order, g, x0, y0, z0 - 1, (int)((z0 + 2) % 3));
+  load_slab(sm, order, g, x0, y0, z0, (int)(z0 % 3));
+
+  const int nvx = TX + 1, nvy = TY + 1;
+  const int ntask = (nvx * nvy + 31) / 32;
+  for (int64_t z = z0; z <= zlast; ++z) {
+    load_slab(sm, order, g, x0, y0, z + 1, (int)((z + 1) % 3));
+    __syncthreads();
+    typedef uint32_t Row[WX];
+    const Row* wm = sm.win[(z + 2) % 3];
+    const Row* w0 = sm.win[z % 3];
+    const Row* wp = sm.win[(z + 1) % 3];
+    for (int task = warp; task < ntask; task += NT / 32) {
+      int idx = task * 32 + lane;
+      if (idx >= nvx * nvy) continue;
+      int lx = idx % nvx, ly = idx / nvx;
+      int64_t x = x0 + lx, y = y0 + ly;
+      if (x >= g.nx || y >= g.ny) continue;
+      const int cx = lx + 1, cy = ly + 1;
+      uint32_t o[14];
+      static_for<0, 14>([&](auto S) {
+        constexpr int s = decltype(S)::value;
+        constexpr int dx = kStar.off[s][0], dy = kStar.off[s][1], dz = kStar.off[s][2];
+        const Row* w = dz < 0 ? wm : (dz > 0 ? wp : w0);
+        o[s] = w[cy + dy][cx + dx];
+      });
+      const uint32_t ox = w0[cy][cx];
+      uint64_t acc[8];
+      int d = lowerstar::process_lower_star<NT>(ox, o, sm.tb, sm.keys, tid, acc);
+      const bool owned = lx < TX && ly < TY && z < zend;
+      if (owned) {
+        desc[x + g.nx * (y + g.ny * z)] = (uint8_t)d;
+        if (d == 15) atomicAdd(&sm.counts[0], 1u);
+      }
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        if (!acc[c]) continue;
+        const int ax = lx - (c & 1), ay = ly - ((c >> 1) & 1);
+        const int64_t az = z - ((c >> 2) & 1);
+        if (ax < 0 || ax >= TX || ay < 0 || ay >= TY || az < z0 || az >= zend) continue;
+        atomicOr(&sm.recs[az & 1][ay][ax], (unsigned long long)acc[c]);
+        const uint64_t a = acc[c];
+        uint32_t ne = __popcll(a & (a >> 1) & (a >> 2) & kEdgeLsb);
+        uint32_t nt = __popcll(a & kTriMask);
+        uint32_t nq = __popcll(a & (a >> 1) & (a >> 2) & kTetLsb);
+        if (ne) atomicAdd(&sm.counts[1], ne);
+        if (nt) atomicAdd(&sm.counts[2], nt);
+        if (nq) atomicAdd(&sm.counts[3], nq);
+      }
+    }
+    __syncthreads();
+    // anchor slab z-1 is complete
+    auto flush = [&](int64_t za) {
+      unsigned long long* buf = &sm.recs[za & 1][0][0];
+      for (int i = tid; i < TX * TY; i += NT) {
+        int ax = i % TX, ay = i / TX;
+        int64_t gx = x0 + ax, gy = y0 + ay;
+        if (gx < g.nx && gy < g.ny) rec[gx + g.nx * (gy + g.ny * za)] = buf[i];
+        buf[i] = 0ull;
+      }
+    };
+    if (z - 1 >= z0) flush(z - 1);
+    if (z == zlast && zlast == zend - 1) {
+      __syncthreads();
+      flush(zlast);
+    }
+    __syncthreads();
+  }
+  if (tid < 4 && sm.counts[tid]) atomicAdd(&counts[tid], (unsigned long long)sm.counts[tid]);
+}
+
+}  // namespace
+
+int launch_gradient(const uint32_t* order, const Grid& g, uint8_t* desc, uint64_t* rec,
+                    int64_t* crit_counts, cudaStream_t s) {
+  static bool configured = false;
+  const size_t smem = sizeof(Smem);
+  if (!configured) {
+    if (cudaFuncSetAttribute(gradient_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return DMS_ERR_CUDA;
+    configured = true;
+  }
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t tx = (g.nx + TX - 1) / TX, ty = (g.ny + TY - 1) / TY;
+  // z chunks: enough CTAs for several waves, chunks of at least 8 slabs
+  int64_t want = (int64_t)sms * 8;
+  int64_t nzc = (want + tx * ty - 1) / (tx * ty);
+  nzc = std::max<int64_t>(1, std::min<int64_t>(nzc, (g.nz + 7) / 8));
+  int zc = (int)((g.nz + nzc - 1) / nzc);
+  nzc = (g.nz + zc - 1) / zc;
+  if (cudaMemsetAsync(crit_counts, 0, 4 * sizeof(int64_t), s) != cudaSuccess) return DMS_ERR_CUDA;
+  dim3 grid((unsigned)tx, (unsigned)ty, (unsigned)nzc);
+  gradient_kernel<<<grid, NT, smem, s>>>(order, g, zc, desc, rec,
+                                         reinterpret_cast<unsigned long long*>(crit_counts)); count_launch();
+  return launch_status();
+}
+
+}  // namespace dms

@@ -1,0 +1,382 @@
+// The global vertex order (Sec. 2.1, Simulation-of-Simplicity tie-break;
+// Sec. 3 "Array Preconditioning"): order[v] = position of v in the stable
+// sort of the vertices by f, with -0.0 == +0.0 and ties left in offset order.
+//
+// A stable least-significant-digit radix sort of 32-bit order-preserving keys
+// with the vertex index as payload, 8-bit digits, reduce-then-scan per pass:
+//   * one pre-pass counts the four digit histograms of the whole field and
+//     flags NaNs; a tiny plan kernel then skips every pass whose digit is the
+//     same for all vertices (quantised fields: the low mantissa bytes), so the
+//     decision never leaves the device;
+//   * per pass: an upsweep counts digits per tile, a three-kernel exclusive
+//     scan turns the (digit-major) tile counts into output offsets, and a
+//     downsweep ranks the tile stably with warp match / popc, stages it in
+//     shared memory in digit order and writes it out;
+//   * the first active pass reads the float field itself (payload = index),
+//     the last one scatters order[payload] = position instead of writing keys.
+#include <algorithm>
+#include <cstdint>
+
+#include "dms_common.cuh"
+
+namespace dms {
+namespace {
+
+constexpr int SORT_NT = 512;
+constexpr int SORT_ITEMS = 16;
+constexpr int SORT_TILE = SORT_NT * SORT_ITEMS;  // 8192
+constexpr int SORT_WARPS = SORT_NT / 32;
+constexpr int SCAN_NT = 1024;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_CHUNK = SCAN_NT * SCAN_ITEMS;
+
+enum : int { SRC_FIELD = 0, SRC_A = 1, SRC_B = 2, DST_A = 1, DST_B = 2, DST_ORDER = 3 };
+
+struct Plan {
+  int active[4];
+  int src[4];
+  int dst[4];
+  int any;
+};
+
+__device__ __forceinline__ uint32_t canon_key(float v, bool* nan) {
+  uint32_t b = __float_as_uint(v);
+  if ((b & 0x7FFFFFFFu) > 0x7F800000u) *nan = true;
+  if (b == 0x80000000u) b = 0u;  // -0.0 sorts as +0.0
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__global__ void __launch_bounds__(256) hist_all_kernel(const float* __restrict__ f, int64_t n,
+                                                       unsigned int* __restrict__ ghist,
+                                                       int32_t* dstatus) {
+  __shared__ unsigned int h[4][256];
+  for (int i = threadIdx.x; i < 1024; i += 256) (&h[0][0])[i] = 0;
+  __syncthreads();
+  bool nan = false;
+  for (int64_t i = blockIdx.x * (int64_t)256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
+    uint32_t k = canon_key(__ldg(f + i), &nan);
+#pragma unroll
+    for (int p = 0; p < 4; ++p) atomicAdd(&h[p][(k >> (8 * p)) & 255u], 1u);
+  }
+  if (__any_sync(0xFFFFFFFFu, nan) && (threadIdx.x & 31) == 0) set_status(dstatus, DMS_ERR_NAN);
+  __syncthreads();
+  for (int i = threadIdx.x; i < 1024; i += 256)
+    if ((&h[0][0])[i]) atomicAdd(ghist + i, (&h[0][0])[i]);
+}
+
+__global__ void plan_kernel(const unsigned int* __restrict__ ghist, int64_t n, Plan* plan) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int act[4];
+  for (int p = 0; p < 4; ++p) {
+    unsigned int mx = 0;
+    for (int d = 0; d < 256; ++d) mx = max(mx, ghist[p * 256 + d]);
+    act[p] = (int64_t)mx != n;
+  }
+  int last = -1, first = -1, cnt = 0;
+  for (int p = 0; p < 4; ++p)
+    if (act[p]) {
+      if (first < 0) first = p;
+      last = p;
+      ++cnt;
+    }
+  int cur = SRC_FIELD, k = 0;
+  for (int p = 0; p < 4; ++p) {
+    plan->active[p] = act[p];
+    plan->src[p] = plan->dst[p] = 0;
+    if (!act[p]) continue;
+    plan->src[p] = cur;
+    int dst = (p == last) ? DST_ORDER : ((k & 1) ? DST_B : DST_A);
+    plan->dst[p] = dst;
+    cur = dst;
+    ++k;
+  }
+  plan->any = cnt > 0;
+}
+
+__device__ __forceinline__ void load_key(int src, const float* f, const uint32_t* ka,
+                                         const uint32_t* kb, int64_t i, uint32_t& k) {
+  bool nan = false;
+  if (src == SRC_FIELD) k = canon_key(__ldg(f + i), &nan);
+  else k = __ldg((src == SRC_A ? ka : kb) + i);
+}
+
+// per-tile digit counts, digit-major: th[d * ntiles + tile]
+__global__ void __launch_bounds__(SORT_NT) upsweep_kernel(int pass, const Plan* __restrict__ plan,
+                                                          const float* __restrict__ f,
+                                                          const uint32_t* __restrict__ ka,
+                                                          const uint32_t* __restrict__ kb,
+                                                          int64_t n, int64_t ntiles,
+                                                          unsigned int* __restrict__ th) {
+  if (!plan->active[pass]) return;
+  const int src = plan->src[pass];
+  __shared__ unsigned int h[SORT_WARPS][256];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < SORT_WARPS * 256; i += SORT_NT) (&h[0][0])[i] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * SORT_TILE + (int64_t)warp * (32 * SORT_ITEMS);
+  for (int r = 0; r < SORT_ITEMS; ++r) {
+    int64_t i = base + r * 32 + lane;
+    uint32_t d = 256u + lane;  // unique dummy digit for the ragged tail
+    if (i < n) {
+      uint32_t k;
+      load_key(src, f, ka, kb, i, k);
+      d = (k >> (8 * pass)) & 255u;
+    }
+    unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
+    if (d < 256u && lane == __ffs(peers) - 1) h[warp][d] += __popc(peers);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < 256; d += SORT_NT) {
+    unsigned int s = 0;
+    for (int w = 0; w < SORT_WARPS; ++w) s += h[w][d];
+    th[(int64_t)d * ntiles + blockIdx.x] = s;
+  }
+}
+
+// exclusive scan of a uint32 array in three kernels (chunk sums, scan of the
+// sums in one CTA, chunk scans with offsets); skipped for inactive passes
+__device__ __forceinline__ unsigned int block_excl_scan(unsigned int v, unsigned int* tmp,
+                                                        unsigned int* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) tmp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned int w = lane < (int)(blockDim.x >> 5) ? tmp[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned int y = __shfl_up_sync(0xFFFFFFFFu, w, o);
+      if (lane >= o) w += y;
+    }
+    tmp[lane] = w;  // inclusive warp totals
+  }
+  __syncthreads();
+  unsigned int excl = x - v + (warp > 0 ? tmp[warp - 1] : 0u);
+  if (total) *total = tmp[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return excl;
+}
+
+__global__ void __launch_bounds__(SCAN_NT) scan_reduce_kernel(int pass, const Plan* plan,
+                                                              const unsigned int* __restrict__ a,
+                                                              int64_t m, unsigned int* sums) {
+  if (plan && !plan->active[pass]) return;
+  __shared__ unsigned int tmp[32];
+  const int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK;
+  unsigned int s = 0;
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    int64_t i = base + (int64_t)k * SCAN_NT + threadIdx.x;
+    if (i < m) s += a[i];
+  }
+  unsigned int total;
+  block_excl_scan(s, tmp, &total);
+  if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(SCAN_NT) scan_sums_kernel(int pass, const Plan* plan,
+                                                            unsigned int* sums, int64_t nsums) {
+  if (plan && !plan->active[pass]) return;
+  __shared__ unsigned int tmp[32];
+  __shared__ unsigned int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t b = 0; b < nsums; b += SCAN_NT) {
+    int64_t i = b + threadIdx.x;
+    unsigned int v = i < nsums ? sums[i] : 0u;
+    unsigned int total;
+    unsigned int e = block_excl_scan(v, tmp, &total);
+    if (i < nsums) sums[i] = e + carry;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += total;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(SCAN_NT) scan_down_kernel(int pass, const Plan* plan,
+                                                            unsigned int* __restrict__ a, int64_t m,
+                                                            const unsigned int* __restrict__ sums) {
+  if (plan && !plan->active[pass]) return;
+  __shared__ unsigned int tmp[32];
+  const int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK + (int64_t)threadIdx.x * SCAN_ITEMS;
+  unsigned int v[SCAN_ITEMS];
+  unsigned int s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    int64_t i = base + k;
+    v[k] = i < m ? a[i] : 0u;
+    s += v[k];
+  }
+  unsigned int e = block_excl_scan(s, tmp, nullptr) + sums[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    int64_t i = base + k;
+    if (i < m) a[i] = e;
+    e += v[k];
+  }
+}
+
+struct DownSmem {
+  unsigned int wh[SORT_WARPS][256];  // per-warp digit counts, then warp offsets
+  unsigned int dstart[256];          // first local position of each digit
+  unsigned int goff[256];            // global offset of each digit for this tile
+  unsigned int tmp[32];
+  uint32_t sk[SORT_TILE];
+  uint32_t sv[SORT_TILE];
+};
+
+__global__ void __launch_bounds__(SORT_NT) downsweep_kernel(
+    int pass, const Plan* __restrict__ plan, const float* __restrict__ f, uint32_t* ka,
+    uint32_t* kb, uint32_t* va, uint32_t* vb, uint32_t* __restrict__ order, int64_t n,
+    int64_t ntiles, const unsigned int* __restrict__ th) {
+  if (!plan->active[pass]) return;
+  const int src = plan->src[pass], dst = plan->dst[pass];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  DownSmem& sm = *reinterpret_cast<DownSmem*>(smem_raw);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int i = threadIdx.x; i < SORT_WARPS * 256; i += SORT_NT) (&sm.wh[0][0])[i] = 0;
+  __syncthreads();
+  const int64_t tile0 = (int64_t)blockIdx.x * SORT_TILE;
+  const int64_t base = tile0 + (int64_t)warp * (32 * SORT_ITEMS);
+  uint32_t key[SORT_ITEMS], val[SORT_ITEMS];
+  unsigned short pos[SORT_ITEMS];
+  const uint32_t* vsrc = src == SRC_A ? va : vb;
+#pragma unroll
+  for (int r = 0; r < SORT_ITEMS; ++r) {
+    int64_t i = base + r * 32 + lane;
+    uint32_t d = 256u + lane;
+    key[r] = 0;
+    val[r] = 0;
+    if (i < n) {
+      load_key(src, f, ka, kb, i, key[r]);
+      val[r] = src == SRC_FIELD ? (uint32_t)i : __ldg(vsrc + i);
+      d = (key[r] >> (8 * pass)) & 255u;
+    }
+    unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
+    unsigned int b = d < 256u ? sm.wh[warp][d] : 0u;
+    __syncwarp();
+    pos[r] = (unsigned short)(b + __popc(peers & lt));
+    if (d < 256u && lane == __ffs(peers) - 1) sm.wh[warp][d] = b + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // warp offsets per digit, digit totals, local digit starts, global offsets
+  unsigned int tot = 0;
+  if (threadIdx.x < 256) {
+    const int d = threadIdx.x;
+    for (int w = 0; w < SORT_WARPS; ++w) {
+      unsigned int c = sm.wh[w][d];
+      sm.wh[w][d] = tot;
+      tot += c;
+    }
+  }
+  unsigned int ds = block_excl_scan(threadIdx.x < 256 ? tot : 0u, sm.tmp, nullptr);
+  if (threadIdx.x < 256) {
+    sm.dstart[threadIdx.x] = ds;
+    sm.goff[threadIdx.x] = th[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < SORT_ITEMS; ++r) {
+    int64_t i = base + r * 32 + lane;
+    if (i < n) {
+      uint32_t d = (key[r] >> (8 * pass)) & 255u;
+      unsigned int p = sm.dstart[d] + sm.wh[warp][d] + pos[r];
+      sm.sk[p] = key[r];
+      sm.sv[p] = val[r];
+    }
+  }
+  __syncthreads();
+  const int64_t cnt = (n - tile0 < (int64_t)SORT_TILE) ? n - tile0 : (int64_t)SORT_TILE;
+  uint32_t* kd = dst == DST_A ? ka : kb;
+  uint32_t* vd = dst == DST_A ? va : vb;
+  for (int p = threadIdx.x; p < cnt; p += SORT_NT) {
+    uint32_t k = sm.sk[p];
+    uint32_t d = (k >> (8 * pass)) & 255u;
+    uint32_t g = sm.goff[d] + (p - sm.dstart[d]);
+    if (dst == DST_ORDER) {
+      order[sm.sv[p]] = g;
+    } else {
+      kd[g] = k;
+      vd[g] = sm.sv[p];
+    }
+  }
+}
+
+__global__ void identity_kernel(const Plan* __restrict__ plan, uint32_t* order, int64_t n) {
+  if (plan->any) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    order[i] = (uint32_t)i;
+}
+
+struct OrderWs {
+  uint32_t *ka, *kb, *va, *vb;
+  unsigned int* th;
+  unsigned int* sums;
+  unsigned int* ghist;
+  Plan* plan;
+  size_t bytes;
+};
+
+OrderWs carve_order(void* base, int64_t n) {
+  WsCarver c(base);
+  OrderWs w;
+  const int64_t ntiles = (n + SORT_TILE - 1) / SORT_TILE;
+  const int64_t m = ntiles * 256;
+  w.ka = c.take<uint32_t>(n);
+  w.kb = c.take<uint32_t>(n);
+  w.va = c.take<uint32_t>(n);
+  w.vb = c.take<uint32_t>(n);
+  w.th = c.take<unsigned int>(m);
+  w.sums = c.take<unsigned int>((m + SCAN_CHUNK - 1) / SCAN_CHUNK + 1);
+  w.ghist = c.take<unsigned int>(1024);
+  w.plan = c.take<Plan>(1);
+  w.bytes = c.used;
+  return w;
+}
+
+}  // namespace
+
+size_t order_workspace_bytes(const Grid& g) { return carve_order(nullptr, g.n).bytes; }
+
+int launch_order(const float* f, const Grid& g, uint32_t* order, void* ws, int32_t* dstatus,
+                 cudaStream_t s) {
+  const int64_t n = g.n;
+  OrderWs w = carve_order(ws, n);
+  const int64_t ntiles = (n + SORT_TILE - 1) / SORT_TILE;
+  const int64_t m = ntiles * 256;
+  const int64_t nsums = (m + SCAN_CHUNK - 1) / SCAN_CHUNK;
+  static bool configured = false;
+  if (!configured) {
+    if (cudaFuncSetAttribute(downsweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(DownSmem)) != cudaSuccess)
+      return DMS_ERR_CUDA;
+    configured = true;
+  }
+  DMS_CUDA_OK(cudaMemsetAsync(w.ghist, 0, 1024 * sizeof(unsigned int), s));
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t hb = std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
+  hist_all_kernel<<<(unsigned)hb, 256, 0, s>>>(f, n, w.ghist, dstatus); count_launch();
+  plan_kernel<<<1, 32, 0, s>>>(w.ghist, n, w.plan); count_launch();
+  for (int p = 0; p < 4; ++p) {
+    upsweep_kernel<<<(unsigned)ntiles, SORT_NT, 0, s>>>(p, w.plan, f, w.ka, w.kb, n, ntiles, w.th); count_launch();
+    scan_reduce_kernel<<<(unsigned)nsums, SCAN_NT, 0, s>>>(p, w.plan, w.th, m, w.sums); count_launch();
+    scan_sums_kernel<<<1, SCAN_NT, 0, s>>>(p, w.plan, w.sums, nsums); count_launch();
+    scan_down_kernel<<<(unsigned)nsums, SCAN_NT, 0, s>>>(p, w.plan, w.th, m, w.sums); count_launch();
+    downsweep_kernel<<<(unsigned)ntiles, SORT_NT, sizeof(DownSmem), s>>>(
+        p, w.plan, f, w.ka, w.kb, w.va, w.vb, order, n, ntiles, w.th); count_launch();
+  }
+  int64_t ib = std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
+  identity_kernel<<<(unsigned)ib, 256, 0, s>>>(w.plan, order, n); count_launch();
+  return launch_status();
+}
+
+}  // namespace dms

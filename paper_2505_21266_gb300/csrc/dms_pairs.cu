@@ -1,0 +1,604 @@
+// Extremum-saddle persistence pairs D0 and D2 (Sec. 2.5, Alg. 1; Sec. 4.1-4.2).
+//
+// 1. v-path tracing, one thread per critical saddle.  D0: from both vertices
+//    of a critical edge, follow desc[] (vertex -> paired edge -> other vertex)
+//    to a minimum.  D2: from both cofacets of a critical triangle follow the
+//    dual gradient (tet -> its paired facet -> that facet's other cofacet) to
+//    a critical tetrahedron, or to the virtual OUTSIDE node when the path
+//    leaves the grid.  Triplets whose two ends coincide are dropped.
+// 2. Pairing rounds.  Alg. 1 visits the saddles in increasing order and, with
+//    a union-find whose roots are the oldest extremum of each component,
+//    pairs the saddle with the younger root when it joins two components.
+//    Here every round takes, for each current component, its lightest live
+//    saddle; a saddle that is the lightest of BOTH of its components is merged
+//    at once.  Such a saddle meets exactly the components Alg. 1 would have
+//    met at its turn (everything merged so far inside a component is lighter
+//    than every live saddle touching it, and nothing lighter touches it), so
+//    every merge -- and therefore every pair -- is the one Alg. 1 makes;
+//    saddles whose ends already share a root are dropped, as in Alg. 1.
+//    The lightest live saddle overall qualifies, so each round makes progress.
+//    Per round: kernel 1 finds both roots (path halving) and records, per
+//    root, the lightest saddle with one 64-bit atomicMax of
+//    (round << 44 | ~weight); kernel 2 merges the mutual ones and appends the
+//    rest to the next live list.
+// 3. Paired saddles are sorted by weight (stable LSD radix sort) and written
+//    as dms_pair records; birth/death values are copied from the field.
+//
+// Weights and ages are 44-bit integers ordered like the lexicographic keys
+// of Sec. 2.1: (order of the top vertex) followed by the ranks, among the
+// lower neighbours of that top vertex, of the other vertices.
+#include <cstdint>
+
+#include "dms_common.cuh"
+#include "dms_radix.cuh"
+#include "dms_scan.cuh"
+
+namespace dms {
+namespace {
+
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr uint64_t kMask44 = (1ull << 44) - 1;
+constexpr int kCornerOfEdge[7] = {1, 2, 4, 3, 5, 6, 7};
+
+__constant__ int cCornerOfEdge[7] = {1, 2, 4, 3, 5, 6, 7};
+__constant__ int cTriPQ[12][2] = {{1, 3}, {2, 3}, {1, 5}, {4, 5}, {2, 6}, {4, 6},
+                                  {1, 7}, {2, 7}, {4, 7}, {3, 7}, {5, 7}, {6, 7}};
+__constant__ int cTetC[6][2] = {{1, 3}, {1, 5}, {2, 3}, {2, 6}, {4, 5}, {4, 6}};
+// neighbour slots: +c for s < 7, -c for s >= 7, c = corner of edge type s % 7
+__constant__ int cSlotCorner[14] = {1, 2, 4, 3, 5, 6, 7, 1, 2, 4, 3, 5, 6, 7};
+
+struct Dev {
+  Grid g;
+  int64_t slot_delta[14];
+};
+
+__device__ __forceinline__ int64_t corner_delta(const Grid& g, int c) {
+  return (c & 1) + ((c >> 1) & 1) * g.nx + ((c >> 2) & 1) * g.sxy;
+}
+__device__ __forceinline__ void xyz(const Grid& g, int64_t v, int64_t& x, int64_t& y, int64_t& z) {
+  z = v / g.sxy;
+  int64_t r = v - z * g.sxy;
+  y = r / g.nx;
+  x = r - y * g.nx;
+}
+// is anchor + corner c inside the grid, for c in {0..7} with all of +c
+__device__ __forceinline__ bool fits(const Grid& g, int64_t ax, int64_t ay, int64_t az, int c) {
+  return ax >= 0 && ay >= 0 && az >= 0 && ax + (c & 1) < g.nx && ay + ((c >> 1) & 1) < g.ny &&
+         az + ((c >> 2) & 1) < g.nz;
+}
+
+// rank of neighbour u among the lower neighbours of its top vertex t
+__device__ __forceinline__ uint32_t local_rank(const Dev& D, const uint32_t* __restrict__ order,
+                                               int64_t t, uint32_t ou) {
+  int64_t x, y, z;
+  xyz(D.g, t, x, y, z);
+  uint32_t r = 0;
+#pragma unroll
+  for (int s = 0; s < 14; ++s) {
+    int c = cSlotCorner[s];
+    int sg = s < 7 ? 1 : -1;
+    int64_t nx = x + sg * (c & 1), ny = y + sg * ((c >> 1) & 1), nz = z + sg * ((c >> 2) & 1);
+    if (nx < 0 || ny < 0 || nz < 0 || nx >= D.g.nx || ny >= D.g.ny || nz >= D.g.nz) continue;
+    r += __ldg(order + t + D.slot_delta[s]) < ou ? 1u : 0u;
+  }
+  return r;
+}
+
+__device__ __forceinline__ int64_t descend(const Dev& D, const uint8_t* __restrict__ desc,
+                                           int64_t v, int32_t* dstatus) {
+  for (int64_t it = 0; it < D.g.n; ++it) {
+    uint8_t d = __ldg(desc + v);
+    if (d >= 14) return v;
+    v += D.slot_delta[d];
+  }
+  set_status(dstatus, DMS_ERR_TIMEOUT);
+  return v;
+}
+
+__device__ __forceinline__ int tet_type(int c1, int c2) {
+  for (int k = 0; k < 6; ++k)
+    if (cTetC[k][0] == c1 && cTetC[k][1] == c2) return k;
+  return -1;
+}
+
+// ascending dual v-path from tet t; -1 = OUTSIDE
+__device__ __forceinline__ int64_t ascend(const Dev& D, const uint64_t* __restrict__ rec, int64_t t,
+                                          int32_t* dstatus) {
+  for (int64_t it = 0; it < 6 * D.g.n; ++it) {
+    int64_t b = t / 6;
+    int k = (int)(t - b * 6);
+    uint32_t code = (uint32_t)(__ldg(rec + b) >> (33 + 3 * k)) & 7u;
+    if (code == 7u) return t;
+    if (code < 1u || code > 4u) {
+      set_status(dstatus, DMS_ERR_ARG);
+      return -1;
+    }
+    const int c1 = cTetC[k][0], c2 = cTetC[k][1];
+    int64_t bx, by, bz;
+    xyz(D.g, b, bx, by, bz);
+    int64_t nb;
+    int n1, n2;
+    switch (code - 1) {
+      case 0: {  // omitted the anchor: the other tet sits one step up
+        bx += c1 & 1;
+        by += (c1 >> 1) & 1;
+        bz += (c1 >> 2) & 1;
+        n1 = c2 ^ c1;
+        n2 = 7 ^ c1;
+        break;
+      }
+      case 3: {  // omitted the top: the other tet sits one step down
+        int e = 7 ^ c2;
+        bx -= e & 1;
+        by -= (e >> 1) & 1;
+        bz -= (e >> 2) & 1;
+        n1 = e;
+        n2 = e | c1;
+        break;
+      }
+      case 1:
+        n1 = c2 ^ c1;
+        n2 = c2;
+        break;
+      default:
+        n1 = c1;
+        n2 = c1 | (7 ^ c2);
+        break;
+    }
+    if (!fits(D.g, bx, by, bz, 7)) return -1;
+    nb = bx + D.g.nx * (by + D.g.ny * bz);
+    t = nb * 6 + tet_type(n1, n2);
+  }
+  set_status(dstatus, DMS_ERR_TIMEOUT);
+  return -1;
+}
+
+__device__ __forceinline__ int64_t bsearch(const int64_t* __restrict__ a, int64_t n, int64_t key) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (__ldg(a + mid) < key) lo = mid + 1;
+    else hi = mid;
+  }
+  return (lo < n && __ldg(a + lo) == key) ? lo : -1;
+}
+
+__device__ __forceinline__ void append(uint32_t* list, unsigned int* count, uint32_t v) {
+  unsigned int active = __activemask();
+  int lane = threadIdx.x & 31;
+  int leader = __ffs(active) - 1;
+  unsigned int base = 0;
+  if (lane == leader) base = atomicAdd(count, __popc(active));
+  base = __shfl_sync(active, base, leader);
+  list[base + __popc(active & ((1u << lane) - 1u))] = v;
+}
+
+struct Tri {
+  uint64_t* w;
+  uint32_t *na, *nb, *ra, *rb, *res;
+};
+
+__global__ void d0_triplets(Dev D, const uint32_t* __restrict__ order,
+                            const uint8_t* __restrict__ desc, const int64_t* __restrict__ crit0,
+                            int64_t nmin, const int64_t* __restrict__ crit1, int64_t ne, Tri T,
+                            uint32_t* live, unsigned int* live_n, int32_t* dstatus) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= ne) return;
+  int64_t id = crit1[i];
+  int64_t a = id / 7;
+  int k = (int)(id - a * 7);
+  int64_t b = a + corner_delta(D.g, cCornerOfEdge[k]);
+  uint32_t oa = __ldg(order + a), ob = __ldg(order + b);
+  int64_t top = oa > ob ? a : b;
+  uint32_t r = local_rank(D, order, top, oa > ob ? ob : oa);
+  T.w[i] = ((uint64_t)(oa > ob ? oa : ob) << 4) | r;
+  T.res[i] = kNone;
+  int64_t t0 = descend(D, desc, a, dstatus), t1 = descend(D, desc, b, dstatus);
+  if (t0 == t1) return;
+  int64_t n0 = bsearch(crit0, nmin, t0), n1 = bsearch(crit0, nmin, t1);
+  if (n0 < 0 || n1 < 0) {
+    set_status(dstatus, DMS_ERR_ARG);
+    return;
+  }
+  T.na[i] = (uint32_t)n0;
+  T.nb[i] = (uint32_t)n1;
+  append(live, live_n, (uint32_t)i);
+}
+
+__global__ void d2_triplets(Dev D, const uint32_t* __restrict__ order,
+                            const uint64_t* __restrict__ rec, const int64_t* __restrict__ crit3,
+                            int64_t nmax, const int64_t* __restrict__ crit2, int64_t nt, Tri T,
+                            uint32_t* live, unsigned int* live_n, int32_t* dstatus) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nt) return;
+  int64_t id = crit2[i];
+  int64_t a = id / 12;
+  int k = (int)(id - a * 12);
+  const int p = cTriPQ[k][0], q = cTriPQ[k][1];
+  // weight: decreasing triangle key
+  int64_t v[3] = {a, a + corner_delta(D.g, p), a + corner_delta(D.g, q)};
+  uint32_t o[3] = {__ldg(order + v[0]), __ldg(order + v[1]), __ldg(order + v[2])};
+  int it = 0;
+  if (o[1] > o[it]) it = 1;
+  if (o[2] > o[it]) it = 2;
+  uint32_t om = 0, ol = 0xFFFFFFFFu;
+  for (int j = 0; j < 3; ++j)
+    if (j != it) {
+      om = max(om, o[j]);
+      ol = min(ol, o[j]);
+    }
+  uint32_t rm = local_rank(D, order, v[it], om), rl = local_rank(D, order, v[it], ol);
+  uint64_t key = ((uint64_t)o[it] << 8) | (rm << 4) | rl;
+  T.w[i] = kMask44 - key;
+  T.res[i] = kNone;
+  // the two cofacets
+  int64_t ax, ay, az;
+  xyz(D.g, a, ax, ay, az);
+  int64_t cof[2] = {-1, -1};
+  if (q == 7) {
+    int e = (__popc(p) == 1) ? (7 ^ p) : p;
+    int e1 = e & -e, e2 = e ^ e1;
+    if (fits(D.g, ax, ay, az, 7)) {
+      if (__popc(p) == 1) {
+        cof[0] = a * 6 + tet_type(p, p | e1);
+        cof[1] = a * 6 + tet_type(p, p | e2);
+      } else {
+        cof[0] = a * 6 + tet_type(e1, p);
+        cof[1] = a * 6 + tet_type(e2, p);
+      }
+    }
+  } else {
+    if (fits(D.g, ax, ay, az, 7)) cof[0] = a * 6 + tet_type(p, q);
+    int e = 7 ^ q;
+    int64_t bx = ax - (e & 1), by = ay - ((e >> 1) & 1), bz = az - ((e >> 2) & 1);
+    if (fits(D.g, bx, by, bz, 7)) cof[1] = (bx + D.g.nx * (by + D.g.ny * bz)) * 6 + tet_type(e, e | p);
+  }
+  int64_t end[2];
+  for (int j = 0; j < 2; ++j) end[j] = cof[j] < 0 ? -1 : ascend(D, rec, cof[j], dstatus);
+  if (end[0] == end[1]) return;
+  int64_t node[2];
+  for (int j = 0; j < 2; ++j) {
+    if (end[j] < 0) {
+      node[j] = 0;
+    } else {
+      int64_t pos = bsearch(crit3, nmax, end[j]);
+      if (pos < 0) {
+        set_status(dstatus, DMS_ERR_ARG);
+        return;
+      }
+      node[j] = pos + 1;
+    }
+  }
+  T.na[i] = (uint32_t)node[0];
+  T.nb[i] = (uint32_t)node[1];
+  append(live, live_n, (uint32_t)i);
+}
+
+__global__ void init_nodes_d0(const uint32_t* __restrict__ order, const int64_t* __restrict__ crit0,
+                              int64_t nmin, uint32_t* parent, unsigned long long* best,
+                              uint64_t* age) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nmin) return;
+  parent[i] = (uint32_t)i;
+  best[i] = 0ull;
+  age[i] = __ldg(order + crit0[i]);
+}
+
+__global__ void init_nodes_d2(Dev D, const uint32_t* __restrict__ order,
+                              const int64_t* __restrict__ crit3, int64_t nmax, uint32_t* parent,
+                              unsigned long long* best, uint64_t* age) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i > nmax) return;
+  parent[i] = (uint32_t)i;
+  best[i] = 0ull;
+  if (i == 0) {
+    age[0] = 0;  // OUTSIDE is older than every maximum
+    return;
+  }
+  int64_t id = crit3[i - 1];
+  int64_t a = id / 6;
+  int k = (int)(id - a * 6);
+  int cs[4] = {0, cTetC[k][0], cTetC[k][1], 7};
+  int64_t v[4];
+  uint32_t o[4];
+  int it = 0;
+  for (int j = 0; j < 4; ++j) {
+    v[j] = a + corner_delta(D.g, cs[j]);
+    o[j] = __ldg(order + v[j]);
+    if (o[j] > o[it]) it = j;
+  }
+  uint32_t r[3];
+  int n = 0;
+  for (int j = 0; j < 4; ++j)
+    if (j != it) r[n++] = local_rank(D, order, v[it], o[j]);
+  // sort the three ranks decreasingly
+  uint32_t h = max(r[0], max(r[1], r[2])), l = min(r[0], min(r[1], r[2]));
+  uint32_t m = r[0] + r[1] + r[2] - h - l;
+  uint64_t key = ((uint64_t)o[it] << 12) | (h << 8) | (m << 4) | l;
+  age[i] = (kMask44 - key) + 1;  // a higher maximum is older
+}
+
+__device__ __forceinline__ uint32_t find_root(uint32_t* parent, uint32_t x) {
+  uint32_t p = parent[x];
+  while (p != x) {
+    uint32_t gp = parent[p];
+    if (gp != p) parent[x] = gp;  // path halving: only ever points further up
+    x = gp;
+    p = parent[x];
+  }
+  return x;
+}
+
+__global__ void round_find(const uint32_t* __restrict__ live, const unsigned int* __restrict__ live_n,
+                           Tri T, uint32_t* parent, unsigned long long* best, uint64_t round) {
+  unsigned int n = *live_n;
+  for (unsigned int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    uint32_t i = live[j];
+    uint32_t a = find_root(parent, T.na[i]), b = find_root(parent, T.nb[i]);
+    T.ra[i] = a;
+    T.rb[i] = b;
+    if (a == b) continue;
+    unsigned long long tv = (round << 44) | (kMask44 - T.w[i]);
+    atomicMax(best + a, tv);
+    atomicMax(best + b, tv);
+  }
+}
+
+__global__ void round_merge(const uint32_t* __restrict__ live, const unsigned int* __restrict__ live_n,
+                            Tri T, uint32_t* parent, const unsigned long long* __restrict__ best,
+                            const uint64_t* __restrict__ age, uint64_t round, uint32_t* next,
+                            unsigned int* next_n) {
+  unsigned int n = *live_n;
+  for (unsigned int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    uint32_t i = live[j];
+    uint32_t a = T.ra[i], b = T.rb[i];
+    if (a == b) continue;  // both ends already joined: no pair (Alg. 1, r0 == r1)
+    unsigned long long tv = (round << 44) | (kMask44 - T.w[i]);
+    if (best[a] == tv && best[b] == tv) {
+      uint32_t young = age[a] > age[b] ? a : b;
+      uint32_t old = young == a ? b : a;
+      parent[young] = old;
+      T.res[i] = young;
+    } else {
+      append(next, next_n, i);
+    }
+  }
+}
+
+__global__ void collect_pairs(const Tri T, int64_t nsad, unsigned long long* keys, uint32_t* vals,
+                              unsigned int* count) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nsad) return;
+  if (T.res[i] == kNone) return;
+  unsigned int active = __activemask();
+  int lane = threadIdx.x & 31, leader = __ffs(active) - 1;
+  unsigned int base = 0;
+  if (lane == leader) base = atomicAdd(count, __popc(active));
+  base = __shfl_sync(active, base, leader);
+  unsigned int slot = base + __popc(active & ((1u << lane) - 1u));
+  keys[slot] = T.w[i];
+  vals[slot] = (uint32_t)i;
+}
+
+__device__ __forceinline__ int64_t top_of(const Dev& D, const uint32_t* order, const int64_t* v,
+                                          int m) {
+  int64_t best = v[0];
+  uint32_t ob = __ldg(order + v[0]);
+  for (int j = 1; j < m; ++j) {
+    uint32_t o = __ldg(order + v[j]);
+    if (o > ob) {
+      ob = o;
+      best = v[j];
+    }
+  }
+  return best;
+}
+
+__global__ void write_d0(Dev D, const float* __restrict__ f, const uint32_t* __restrict__ order,
+                         const int64_t* __restrict__ crit0, const int64_t* __restrict__ crit1,
+                         const Tri T, const uint32_t* __restrict__ sorted_idx,
+                         const unsigned int* __restrict__ count, dms_pair* out, int64_t cap,
+                         int64_t* n_out, int32_t* dstatus) {
+  unsigned int n = *count;
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j == 0) {
+    *n_out = n;
+    if ((int64_t)n > cap) set_status(dstatus, DMS_ERR_CAPACITY);
+  }
+  if (j >= n || j >= cap) return;
+  uint32_t i = sorted_idx[j];
+  int64_t m = crit0[T.res[i]];
+  int64_t id = crit1[i];
+  int64_t a = id / 7;
+  int k = (int)(id - a * 7);
+  int64_t v[2] = {a, a + corner_delta(D.g, cCornerOfEdge[k])};
+  int64_t top = top_of(D, order, v, 2);
+  dms_pair p;
+  p.birth_id = m;
+  p.death_id = id;
+  p.birth = __ldg(f + m);
+  p.death = __ldg(f + top);
+  p.birth_vtx = (uint32_t)m;
+  p.death_vtx = (uint32_t)top;
+  out[j] = p;
+}
+
+__global__ void write_d2(Dev D, const float* __restrict__ f, const uint32_t* __restrict__ order,
+                         const int64_t* __restrict__ crit2, const int64_t* __restrict__ crit3,
+                         const Tri T, const uint32_t* __restrict__ sorted_idx,
+                         const unsigned int* __restrict__ count, dms_pair* out, int64_t cap,
+                         int64_t* n_out, int32_t* dstatus) {
+  unsigned int n = *count;
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j == 0) {
+    *n_out = n;
+    if ((int64_t)n > cap) set_status(dstatus, DMS_ERR_CAPACITY);
+  }
+  if (j >= n || j >= cap) return;
+  uint32_t i = sorted_idx[j];
+  int64_t tet = crit3[T.res[i] - 1];  // node 0 (OUTSIDE) never dies
+  int64_t tri = crit2[i];
+  int64_t a = tri / 12;
+  int k = (int)(tri - a * 12);
+  int64_t tv[3] = {a, a + corner_delta(D.g, cTriPQ[k][0]), a + corner_delta(D.g, cTriPQ[k][1])};
+  int64_t b = tet / 6;
+  int kk = (int)(tet - b * 6);
+  int64_t qv[4] = {b, b + corner_delta(D.g, cTetC[kk][0]), b + corner_delta(D.g, cTetC[kk][1]),
+                   b + corner_delta(D.g, 7)};
+  int64_t st = top_of(D, order, tv, 3), qt = top_of(D, order, qv, 4);
+  dms_pair p;
+  p.birth_id = tri;
+  p.death_id = tet;
+  p.birth = __ldg(f + st);
+  p.death = __ldg(f + qt);
+  p.birth_vtx = (uint32_t)st;
+  p.death_vtx = (uint32_t)qt;
+  out[j] = p;
+}
+
+__global__ void write_essential(const float* __restrict__ f, const uint32_t* __restrict__ order,
+                                const int64_t* __restrict__ crit0, int64_t nmin, dms_pair* ess) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nmin) return;
+  int64_t m = crit0[i];
+  if (__ldg(order + m) != 0u) return;  // the global minimum never dies
+  dms_pair p;
+  p.birth_id = m;
+  p.death_id = -1;
+  p.birth = __ldg(f + m);
+  p.death = __int_as_float(0x7F800000);
+  p.birth_vtx = (uint32_t)m;
+  p.death_vtx = 0;
+  *ess = p;
+}
+
+struct DiagWs {
+  Tri T0, T2;
+  uint32_t *live0, *live1;
+  unsigned int* ctr;  // [0..1] live counts, [2] pair count
+  uint32_t* parent;
+  unsigned long long* best;
+  uint64_t* age;
+  radix64::Buffers rb;
+  size_t bytes;
+};
+
+DiagWs carve_diag(void* base, const int64_t* nc) {
+  WsCarver c(base);
+  DiagWs w;
+  const int64_t nsad = std::max<int64_t>(std::max<int64_t>(nc[1], nc[2]), 1);
+  const int64_t nnode = std::max<int64_t>(nc[0], nc[3] + 1);
+  auto tri = [&](Tri& t) {
+    t.w = c.take<uint64_t>(nsad);
+    t.na = c.take<uint32_t>(nsad);
+    t.nb = c.take<uint32_t>(nsad);
+    t.ra = c.take<uint32_t>(nsad);
+    t.rb = c.take<uint32_t>(nsad);
+    t.res = c.take<uint32_t>(nsad);
+  };
+  tri(w.T0);
+  w.T2 = w.T0;  // D0 and D2 run one after the other and share the arrays
+  w.live0 = c.take<uint32_t>(nsad);
+  w.live1 = c.take<uint32_t>(nsad);
+  w.ctr = c.take<unsigned int>(8);
+  w.parent = c.take<uint32_t>(nnode);
+  w.best = c.take<unsigned long long>(nnode);
+  w.age = c.take<uint64_t>(nnode);
+  w.rb = radix64::carve(c, nsad);
+  w.bytes = c.used;
+  return w;
+}
+
+int run_rounds(DiagWs& w, Tri T, cudaStream_t s, int32_t* dstatus) {
+  uint32_t* cur = w.live0;
+  uint32_t* nxt = w.live1;
+  unsigned int* cur_n = w.ctr + 0;
+  unsigned int* nxt_n = w.ctr + 1;
+  for (uint64_t round = 1;; ++round) {
+    unsigned int h = 0;
+    DMS_CUDA_OK(cudaMemcpyAsync(&h, cur_n, sizeof(h), cudaMemcpyDeviceToHost, s));
+    DMS_CUDA_OK(cudaStreamSynchronize(s));
+    if (h == 0) break;
+    if (round >= (1ull << 20) - 1) {
+      return DMS_ERR_TIMEOUT;
+    }
+    unsigned int blocks = (unsigned int)std::min<int64_t>((h + 255) / 256, 1 << 16);
+    DMS_CUDA_OK(cudaMemsetAsync(nxt_n, 0, sizeof(unsigned int), s));
+    round_find<<<blocks, 256, 0, s>>>(cur, cur_n, T, w.parent, w.best, round); count_launch();
+    round_merge<<<blocks, 256, 0, s>>>(cur, cur_n, T, w.parent, w.best, w.age, round, nxt, nxt_n); count_launch();
+    std::swap(cur, nxt);
+    std::swap(cur_n, nxt_n);
+  }
+  (void)dstatus;
+  return launch_status();
+}
+
+}  // namespace
+
+size_t diagram_workspace_bytes(const Grid& g, const int64_t* n_crit) {
+  (void)g;
+  return carve_diag(nullptr, n_crit).bytes;
+}
+
+int launch_diagram(const float* f, const uint32_t* order, const uint8_t* desc, const uint64_t* rec,
+                   const Grid& g, const int64_t* crit0, const int64_t* crit1, const int64_t* crit2,
+                   const int64_t* crit3, const int64_t* nc, dms_pair* d0, int64_t cap0,
+                   dms_pair* d2, int64_t cap2, dms_pair* ess, int64_t* n_out, void* ws,
+                   int32_t* dstatus, cudaStream_t s) {
+  DiagWs w = carve_diag(ws, nc);
+  Dev D;
+  D.g = g;
+  for (int sl = 0; sl < 14; ++sl) {
+    int c = kCornerOfEdge[sl % 7];
+    int64_t d = (c & 1) + ((c >> 1) & 1) * g.nx + ((c >> 2) & 1) * g.sxy;
+    D.slot_delta[sl] = sl < 7 ? d : -d;
+  }
+  const int TB = 256;
+  auto nb = [&](int64_t n) { return (unsigned)std::max<int64_t>(1, (n + TB - 1) / TB); };
+
+  // ---- D0
+  DMS_CUDA_OK(cudaMemsetAsync(w.ctr, 0, 8 * sizeof(unsigned int), s));
+  if (nc[0] > 0) {
+    init_nodes_d0<<<nb(nc[0]), TB, 0, s>>>(order, crit0, nc[0], w.parent, w.best, w.age); count_launch();
+    write_essential<<<nb(nc[0]), TB, 0, s>>>(f, order, crit0, nc[0], ess); count_launch();
+  }
+  if (nc[1] > 0)
+    d0_triplets<<<nb(nc[1]), TB, 0, s>>>(D, order, desc, crit0, nc[0], crit1, nc[1], w.T0,
+                                         w.live0, w.ctr + 0, dstatus); count_launch();
+  int st = run_rounds(w, w.T0, s, dstatus);
+  if (st) return st;
+  if (nc[1] > 0) {
+    collect_pairs<<<nb(nc[1]), TB, 0, s>>>(w.T0, nc[1], w.rb.ka, w.rb.va, w.ctr + 2); count_launch();
+    unsigned int np = 0;
+    DMS_CUDA_OK(cudaMemcpyAsync(&np, w.ctr + 2, sizeof(np), cudaMemcpyDeviceToHost, s));
+    DMS_CUDA_OK(cudaStreamSynchronize(s));
+    bool in_a = radix64::sort(w.rb, np, 36, s);
+    write_d0<<<nb(np), TB, 0, s>>>(D, f, order, crit0, crit1, w.T0, in_a ? w.rb.va : w.rb.vb,
+                                   w.ctr + 2, d0, cap0, n_out + 0, dstatus); count_launch();
+  } else {
+    DMS_CUDA_OK(cudaMemsetAsync(n_out + 0, 0, sizeof(int64_t), s));
+  }
+
+  // ---- D2
+  DMS_CUDA_OK(cudaMemsetAsync(w.ctr, 0, 8 * sizeof(unsigned int), s));
+  init_nodes_d2<<<nb(nc[3] + 1), TB, 0, s>>>(D, order, crit3, nc[3], w.parent, w.best, w.age); count_launch();
+  if (nc[2] > 0)
+    d2_triplets<<<nb(nc[2]), TB, 0, s>>>(D, order, rec, crit3, nc[3], crit2, nc[2], w.T2,
+                                         w.live0, w.ctr + 0, dstatus); count_launch();
+  st = run_rounds(w, w.T2, s, dstatus);
+  if (st) return st;
+  if (nc[2] > 0) {
+    collect_pairs<<<nb(nc[2]), TB, 0, s>>>(w.T2, nc[2], w.rb.ka, w.rb.va, w.ctr + 2); count_launch();
+    unsigned int np = 0;
+    DMS_CUDA_OK(cudaMemcpyAsync(&np, w.ctr + 2, sizeof(np), cudaMemcpyDeviceToHost, s));
+    DMS_CUDA_OK(cudaStreamSynchronize(s));
+    bool in_a = radix64::sort(w.rb, np, 44, s);
+    write_d2<<<nb(np), TB, 0, s>>>(D, f, order, crit2, crit3, w.T2, in_a ? w.rb.va : w.rb.vb,
+                                   w.ctr + 2, d2, cap2, n_out + 1, dstatus); count_launch();
+  } else {
+    DMS_CUDA_OK(cudaMemsetAsync(n_out + 1, 0, sizeof(int64_t), s));
+  }
+  return launch_status();
+}
+
+}  // namespace dms

@@ -212,8 +212,31 @@ def main():
         d = dms.diagram_d0d2(field, o, g, c, status=st)
         return d, st, c
 
+    def staged(field):
+        """One step with a synchronisation after every stage (stderr report)."""
+        st = torch.zeros(1, dtype=torch.int32, device=dev)
+        marks = [time.perf_counter()]
+        o = dms.order(field, status=st)
+        torch.cuda.synchronize()
+        marks.append(time.perf_counter())
+        g = dms.gradient(o)
+        torch.cuda.synchronize()
+        marks.append(time.perf_counter())
+        c = dms.critical(g)
+        torch.cuda.synchronize()
+        marks.append(time.perf_counter())
+        d = dms.diagram_d0d2(field, o, g, c, status=st)
+        torch.cuda.synchronize()
+        marks.append(time.perf_counter())
+        names = ["order", "gradient", "critical", "d0d2"]
+        print("stages ms: " + ", ".join(f"{nm} {1e3 * (b - a):.2f}"
+                                        for nm, a, b in zip(names, marks, marks[1:])),
+              file=sys.stderr, flush=True)
+        return d, st, c
+
+    print(f"field ready: {nvert} vertices", file=sys.stderr, flush=True)
     for _ in range(args.warmup):
-        d, st, c = step(f)
+        d, st, c = staged(f)
     torch.cuda.synchronize()
     if int(st.item()) != 0:
         raise RuntimeError(f"device status {int(st.item())}")

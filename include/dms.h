@@ -158,14 +158,15 @@ int dms_critical(const uint8_t* desc, const uint64_t* rec, dms_dims d, int64_t* 
  * two cofacets of every critical triangle the dual (ascending) v-path is
  * followed to a critical tetrahedron, or to a virtual OUTSIDE node when the
  * path leaves the grid; triangles are taken in decreasing order and the lower
- * maximum dies (OUTSIDE never dies).  The pairing rounds are exact: each
- * round merges the saddles that are the lightest live saddle of both of
- * their components, which is the order Alg. 1 would have used on them.
+ * maximum dies (OUTSIDE never dies).  The pairing runs in rounds that are
+ * exact: a round merges every saddle that is the lightest live saddle of both
+ * of its components, or the lightest of a component whose other side is
+ * older; both choices are the ones Alg. 1 makes at that saddle's turn.
  *   f, order, desc, rec   as above;  crit0..3 and n_crit (HOST array of 4)
  *                         from dms_critical.
- *   d0   [cap0] out: D0 pairs in increasing edge order (n_crit[0]-1 of them
- *        for a grid, plus the essential class written to *d0_essential).
- *   d2   [cap2] out: D2 pairs in decreasing triangle order (n_crit[3]).
+ *   d0   [cap0] out: D0 pairs in increasing edge-id order (n_crit[0]-1 of
+ *        them for a grid, plus the essential class written to *d0_essential).
+ *   d2   [cap2] out: D2 pairs in increasing triangle-id order (n_crit[3]).
  *   n_out [2] int64 out: numbers of D0 and D2 pairs (capacity errors as in
  *        dms_critical).
  *   ws   at least dms_diagram_workspace_size(d, n_crit) bytes.

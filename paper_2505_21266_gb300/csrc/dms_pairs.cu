@@ -21,8 +21,9 @@
 //    root, the lightest saddle with one 64-bit atomicMax of
 //    (round << 44 | ~weight); kernel 2 merges the mutual ones and appends the
 //    rest to the next live list.
-// 3. Paired saddles are sorted by weight (stable LSD radix sort) and written
-//    as dms_pair records; birth/death values are copied from the field.
+// 3. Paired saddles are compacted in saddle-id order (block scans plus one
+//    device-wide scan) and written as dms_pair records; birth/death values
+//    are copied from the field.
 //
 // Weights and ages are 44-bit integers ordered like the lexicographic keys
 // of Sec. 2.1: (order of the top vertex) followed by the ranks, among the
@@ -344,6 +345,16 @@ __global__ void round_find(const uint32_t* __restrict__ live, const unsigned int
   }
 }
 
+// Merge rules, each exact (see the header comment):
+//  * mutual: the saddle is the lightest live saddle of both components -> the
+//    younger root dies;
+//  * downhill: the saddle is the lightest live saddle of component a and the
+//    other component b is older -> a's root dies.  At the saddle's turn in
+//    Alg. 1 a's component is exactly a (nothing lighter touches it, and every
+//    merge that built a used a lighter saddle), while b's side already holds
+//    b's root, which is older than a's, so a's root is the younger one.
+// A root dies through its own lightest saddle only, so it dies at most once
+// per round, and the links never form a cycle (each points to an older root).
 __global__ void round_merge(const uint32_t* __restrict__ live, const unsigned int* __restrict__ live_n,
                             Tri T, uint32_t* parent, const unsigned long long* __restrict__ best,
                             const uint64_t* __restrict__ age, uint64_t round, uint32_t* next,
@@ -354,9 +365,20 @@ __global__ void round_merge(const uint32_t* __restrict__ live, const unsigned in
     uint32_t a = T.ra[i], b = T.rb[i];
     if (a == b) continue;  // both ends already joined: no pair (Alg. 1, r0 == r1)
     unsigned long long tv = (round << 44) | (kMask44 - T.w[i]);
-    if (best[a] == tv && best[b] == tv) {
-      uint32_t young = age[a] > age[b] ? a : b;
-      uint32_t old = young == a ? b : a;
+    const bool la = best[a] == tv, lb = best[b] == tv;
+    const uint64_t ga = age[a], gb = age[b];
+    uint32_t young = kNone, old = kNone;
+    if (la && lb) {
+      young = ga > gb ? a : b;
+      old = young == a ? b : a;
+    } else if (la && ga > gb) {
+      young = a;
+      old = b;
+    } else if (lb && gb > ga) {
+      young = b;
+      old = a;
+    }
+    if (young != kNone) {
       parent[young] = old;
       T.res[i] = young;
     } else {
@@ -365,19 +387,49 @@ __global__ void round_merge(const uint32_t* __restrict__ live, const unsigned in
   }
 }
 
-__global__ void collect_pairs(const Tri T, int64_t nsad, unsigned long long* keys, uint32_t* vals,
-                              unsigned int* count) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= nsad) return;
-  if (T.res[i] == kNone) return;
-  unsigned int active = __activemask();
-  int lane = threadIdx.x & 31, leader = __ffs(active) - 1;
-  unsigned int base = 0;
-  if (lane == leader) base = atomicAdd(count, __popc(active));
-  base = __shfl_sync(active, base, leader);
-  unsigned int slot = base + __popc(active & ((1u << lane) - 1u));
-  keys[slot] = T.w[i];
-  vals[slot] = (uint32_t)i;
+// The last few live saddles, processed one by one in increasing weight: the
+// lightest live saddle is always the lightest of both of its components, so
+// this continues Alg. 1 exactly.
+__global__ void gather_live(const uint32_t* __restrict__ live, const unsigned int* __restrict__ live_n,
+                            const Tri T, unsigned long long* keys, uint32_t* vals) {
+  unsigned int n = *live_n;
+  for (unsigned int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    keys[j] = T.w[live[j]];
+    vals[j] = live[j];
+  }
+}
+
+__global__ void sequential_finish(const uint32_t* __restrict__ sorted, const unsigned int* __restrict__ live_n,
+                                  Tri T, uint32_t* parent, const uint64_t* __restrict__ age) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  unsigned int n = *live_n;
+  for (unsigned int j = 0; j < n; ++j) {
+    uint32_t i = sorted[j];
+    uint32_t a = T.na[i], b = T.nb[i];
+    while (parent[a] != a) a = parent[a] = parent[parent[a]];
+    while (parent[b] != b) b = parent[b] = parent[parent[b]];
+    if (a == b) continue;
+    uint32_t young = age[a] > age[b] ? a : b;
+    uint32_t old = young == a ? b : a;
+    parent[young] = old;
+    T.res[i] = young;
+  }
+}
+
+// ordered compaction of the paired saddles (kept in saddle-id order)
+constexpr int PNT = 256, PITEMS = 16, PTILE = PNT * PITEMS;
+
+__global__ void __launch_bounds__(PNT) count_pairs(const Tri T, int64_t nsad, long long* tc) {
+  __shared__ long long tmp[32];
+  const int64_t base = (int64_t)blockIdx.x * PTILE + (int64_t)threadIdx.x * PITEMS;
+  int c = 0;
+  for (int k = 0; k < PITEMS; ++k) {
+    int64_t i = base + k;
+    if (i < nsad && T.res[i] != kNone) ++c;
+  }
+  long long t;
+  scan64::block_excl(c, tmp, &t);
+  if (threadIdx.x == 0) tc[blockIdx.x] = t;
 }
 
 __device__ __forceinline__ int64_t top_of(const Dev& D, const uint32_t* order, const int64_t* v,
@@ -394,19 +446,9 @@ __device__ __forceinline__ int64_t top_of(const Dev& D, const uint32_t* order, c
   return best;
 }
 
-__global__ void write_d0(Dev D, const float* __restrict__ f, const uint32_t* __restrict__ order,
-                         const int64_t* __restrict__ crit0, const int64_t* __restrict__ crit1,
-                         const Tri T, const uint32_t* __restrict__ sorted_idx,
-                         const unsigned int* __restrict__ count, dms_pair* out, int64_t cap,
-                         int64_t* n_out, int32_t* dstatus) {
-  unsigned int n = *count;
-  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (j == 0) {
-    *n_out = n;
-    if ((int64_t)n > cap) set_status(dstatus, DMS_ERR_CAPACITY);
-  }
-  if (j >= n || j >= cap) return;
-  uint32_t i = sorted_idx[j];
+__device__ __forceinline__ void write_one_d0(const Dev& D, const float* f, const uint32_t* order,
+                                            const int64_t* crit0, const int64_t* crit1,
+                                            const Tri& T, int64_t i, dms_pair* out) {
   int64_t m = crit0[T.res[i]];
   int64_t id = crit1[i];
   int64_t a = id / 7;
@@ -420,22 +462,12 @@ __global__ void write_d0(Dev D, const float* __restrict__ f, const uint32_t* __r
   p.death = __ldg(f + top);
   p.birth_vtx = (uint32_t)m;
   p.death_vtx = (uint32_t)top;
-  out[j] = p;
+  *out = p;
 }
 
-__global__ void write_d2(Dev D, const float* __restrict__ f, const uint32_t* __restrict__ order,
-                         const int64_t* __restrict__ crit2, const int64_t* __restrict__ crit3,
-                         const Tri T, const uint32_t* __restrict__ sorted_idx,
-                         const unsigned int* __restrict__ count, dms_pair* out, int64_t cap,
-                         int64_t* n_out, int32_t* dstatus) {
-  unsigned int n = *count;
-  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (j == 0) {
-    *n_out = n;
-    if ((int64_t)n > cap) set_status(dstatus, DMS_ERR_CAPACITY);
-  }
-  if (j >= n || j >= cap) return;
-  uint32_t i = sorted_idx[j];
+__device__ __forceinline__ void write_one_d2(const Dev& D, const float* f, const uint32_t* order,
+                                            const int64_t* crit2, const int64_t* crit3,
+                                            const Tri& T, int64_t i, dms_pair* out) {
   int64_t tet = crit3[T.res[i] - 1];  // node 0 (OUTSIDE) never dies
   int64_t tri = crit2[i];
   int64_t a = tri / 12;
@@ -453,7 +485,39 @@ __global__ void write_d2(Dev D, const float* __restrict__ f, const uint32_t* __r
   p.death = __ldg(f + qt);
   p.birth_vtx = (uint32_t)st;
   p.death_vtx = (uint32_t)qt;
-  out[j] = p;
+  *out = p;
+}
+
+// dim 0 -> D0 records, dim 2 -> D2 records, in saddle-id order
+__global__ void __launch_bounds__(PNT) write_pairs(int dim, Dev D, const float* __restrict__ f,
+                                                   const uint32_t* __restrict__ order,
+                                                   const int64_t* __restrict__ critA,
+                                                   const int64_t* __restrict__ critB, const Tri T,
+                                                   int64_t nsad, const long long* __restrict__ toff,
+                                                   const long long* __restrict__ total,
+                                                   dms_pair* out, int64_t cap, int64_t* n_out,
+                                                   int32_t* dstatus) {
+  __shared__ long long tmp[32];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *n_out = *total;
+    if (*total > cap) set_status(dstatus, DMS_ERR_CAPACITY);
+  }
+  const int64_t base = (int64_t)blockIdx.x * PTILE + (int64_t)threadIdx.x * PITEMS;
+  int c = 0;
+  for (int k = 0; k < PITEMS; ++k) {
+    int64_t i = base + k;
+    if (i < nsad && T.res[i] != kNone) ++c;
+  }
+  long long pos = scan64::block_excl(c, tmp, nullptr) + toff[blockIdx.x];
+  for (int k = 0; k < PITEMS; ++k) {
+    int64_t i = base + k;
+    if (i >= nsad || T.res[i] == kNone) continue;
+    if (pos < cap) {
+      if (dim == 0) write_one_d0(D, f, order, critA, critB, T, i, out + pos);
+      else write_one_d2(D, f, order, critA, critB, T, i, out + pos);
+    }
+    ++pos;
+  }
 }
 
 __global__ void write_essential(const float* __restrict__ f, const uint32_t* __restrict__ order,
@@ -504,24 +568,33 @@ DiagWs carve_diag(void* base, const int64_t* nc) {
   w.parent = c.take<uint32_t>(nnode);
   w.best = c.take<unsigned long long>(nnode);
   w.age = c.take<uint64_t>(nnode);
-  w.rb = radix64::carve(c, nsad);
+  w.rb = radix64::carve(c, std::max<int64_t>(nsad, 4096));
   w.bytes = c.used;
   return w;
 }
+
+constexpr unsigned int kSeqMax = 4096;  // live saddles left to the sequential finish
 
 int run_rounds(DiagWs& w, Tri T, cudaStream_t s, int32_t* dstatus) {
   uint32_t* cur = w.live0;
   uint32_t* nxt = w.live1;
   unsigned int* cur_n = w.ctr + 0;
   unsigned int* nxt_n = w.ctr + 1;
+  unsigned int prev = 0xFFFFFFFFu;
   for (uint64_t round = 1;; ++round) {
     unsigned int h = 0;
     DMS_CUDA_OK(cudaMemcpyAsync(&h, cur_n, sizeof(h), cudaMemcpyDeviceToHost, s));
     DMS_CUDA_OK(cudaStreamSynchronize(s));
     if (h == 0) break;
-    if (round >= (1ull << 20) - 1) {
-      return DMS_ERR_TIMEOUT;
+    if ((h <= kSeqMax && (uint64_t)h * 4 > (uint64_t)prev * 3) || round >= (1ull << 20) - 2) {
+      // few saddles left and the rounds have stalled: finish in sorted order
+      unsigned int blocks = (h + 255) / 256;
+      gather_live<<<blocks, 256, 0, s>>>(cur, cur_n, T, w.rb.ka, w.rb.va); count_launch();
+      bool in_a = radix64::sort(w.rb, h, 44, s);
+      sequential_finish<<<1, 32, 0, s>>>(in_a ? w.rb.va : w.rb.vb, cur_n, T, w.parent, w.age); count_launch();
+      break;
     }
+    prev = h;
     unsigned int blocks = (unsigned int)std::min<int64_t>((h + 255) / 256, 1 << 16);
     DMS_CUDA_OK(cudaMemsetAsync(nxt_n, 0, sizeof(unsigned int), s));
     round_find<<<blocks, 256, 0, s>>>(cur, cur_n, T, w.parent, w.best, round); count_launch();
@@ -530,6 +603,24 @@ int run_rounds(DiagWs& w, Tri T, cudaStream_t s, int32_t* dstatus) {
     std::swap(cur_n, nxt_n);
   }
   (void)dstatus;
+  return launch_status();
+}
+
+int write_diagram(int dim, DiagWs& w, const Dev& D, const float* f, const uint32_t* order,
+                  const int64_t* critA, const int64_t* critB, int64_t nsad, dms_pair* out,
+                  int64_t cap, int64_t* n_out, int32_t* dstatus, cudaStream_t s) {
+  if (nsad <= 0) {
+    DMS_CUDA_OK(cudaMemsetAsync(n_out, 0, sizeof(int64_t), s));
+    return DMS_OK;
+  }
+  const int64_t ntiles = (nsad + PTILE - 1) / PTILE;
+  long long* tc = reinterpret_cast<long long*>(w.rb.ka);
+  long long* sums = reinterpret_cast<long long*>(w.rb.kb);
+  count_pairs<<<(unsigned)ntiles, PNT, 0, s>>>(w.T0, nsad, tc); count_launch();
+  scan64::run(tc, ntiles, sums, s);
+  write_pairs<<<(unsigned)ntiles, PNT, 0, s>>>(dim, D, f, order, critA, critB, w.T0, nsad, tc,
+                                               sums + scan64::num_sums(ntiles), out, cap, n_out,
+                                               dstatus); count_launch();
   return launch_status();
 }
 
@@ -562,42 +653,26 @@ int launch_diagram(const float* f, const uint32_t* order, const uint8_t* desc, c
     init_nodes_d0<<<nb(nc[0]), TB, 0, s>>>(order, crit0, nc[0], w.parent, w.best, w.age); count_launch();
     write_essential<<<nb(nc[0]), TB, 0, s>>>(f, order, crit0, nc[0], ess); count_launch();
   }
-  if (nc[1] > 0)
+  if (nc[1] > 0) {
     d0_triplets<<<nb(nc[1]), TB, 0, s>>>(D, order, desc, crit0, nc[0], crit1, nc[1], w.T0,
                                          w.live0, w.ctr + 0, dstatus); count_launch();
+  }
   int st = run_rounds(w, w.T0, s, dstatus);
   if (st) return st;
-  if (nc[1] > 0) {
-    collect_pairs<<<nb(nc[1]), TB, 0, s>>>(w.T0, nc[1], w.rb.ka, w.rb.va, w.ctr + 2); count_launch();
-    unsigned int np = 0;
-    DMS_CUDA_OK(cudaMemcpyAsync(&np, w.ctr + 2, sizeof(np), cudaMemcpyDeviceToHost, s));
-    DMS_CUDA_OK(cudaStreamSynchronize(s));
-    bool in_a = radix64::sort(w.rb, np, 36, s);
-    write_d0<<<nb(np), TB, 0, s>>>(D, f, order, crit0, crit1, w.T0, in_a ? w.rb.va : w.rb.vb,
-                                   w.ctr + 2, d0, cap0, n_out + 0, dstatus); count_launch();
-  } else {
-    DMS_CUDA_OK(cudaMemsetAsync(n_out + 0, 0, sizeof(int64_t), s));
-  }
+  st = write_diagram(0, w, D, f, order, crit0, crit1, nc[1], d0, cap0, n_out + 0, dstatus, s);
+  if (st) return st;
 
   // ---- D2
   DMS_CUDA_OK(cudaMemsetAsync(w.ctr, 0, 8 * sizeof(unsigned int), s));
   init_nodes_d2<<<nb(nc[3] + 1), TB, 0, s>>>(D, order, crit3, nc[3], w.parent, w.best, w.age); count_launch();
-  if (nc[2] > 0)
+  if (nc[2] > 0) {
     d2_triplets<<<nb(nc[2]), TB, 0, s>>>(D, order, rec, crit3, nc[3], crit2, nc[2], w.T2,
                                          w.live0, w.ctr + 0, dstatus); count_launch();
+  }
   st = run_rounds(w, w.T2, s, dstatus);
   if (st) return st;
-  if (nc[2] > 0) {
-    collect_pairs<<<nb(nc[2]), TB, 0, s>>>(w.T2, nc[2], w.rb.ka, w.rb.va, w.ctr + 2); count_launch();
-    unsigned int np = 0;
-    DMS_CUDA_OK(cudaMemcpyAsync(&np, w.ctr + 2, sizeof(np), cudaMemcpyDeviceToHost, s));
-    DMS_CUDA_OK(cudaStreamSynchronize(s));
-    bool in_a = radix64::sort(w.rb, np, 44, s);
-    write_d2<<<nb(np), TB, 0, s>>>(D, f, order, crit2, crit3, w.T2, in_a ? w.rb.va : w.rb.vb,
-                                   w.ctr + 2, d2, cap2, n_out + 1, dstatus); count_launch();
-  } else {
-    DMS_CUDA_OK(cudaMemsetAsync(n_out + 1, 0, sizeof(int64_t), s));
-  }
+  st = write_diagram(2, w, D, f, order, crit2, crit3, nc[2], d2, cap2, n_out + 1, dstatus, s);
+  if (st) return st;
   return launch_status();
 }
 

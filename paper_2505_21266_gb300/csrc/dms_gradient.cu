@@ -30,12 +30,11 @@
 namespace dms {
 namespace {
 
-constexpr int TX = 32, TY = 32;
+constexpr int TX = 32, TY = 24;
 constexpr int WX = TX + 3, WY = TY + 3;
 constexpr int NT = 256;
-constexpr int NKEYS = 14 + 36 + 24;
 
-__constant__ StarTables cStar = kStar;
+__constant__ lowerstar::Tables cTables = lowerstar::make_tables();
 
 using lowerstar::static_for;
 
@@ -47,7 +46,7 @@ struct Smem {
   lowerstar::Tables tb;
   uint32_t win[3][WY][WX];
   unsigned long long recs[2][TY][TX];
-  uint16_t keys[NKEYS][NT];
+  lowerstar::Keys<NT> keys;
   unsigned int counts[4];
 };
 
@@ -63,7 +62,7 @@ __device__ __forceinline__ void load_slab(Smem& sm, const uint32_t* __restrict__
   }
 }
 
-__global__ void __launch_bounds__(NT) gradient_kernel(const uint32_t* __restrict__ order, Grid g,
+__global__ void __launch_bounds__(NT, 4) gradient_kernel(const uint32_t* __restrict__ order, Grid g,
                                                       int zc, uint8_t* __restrict__ desc,
                                                       uint64_t* __restrict__ rec,
                                                       unsigned long long* __restrict__ counts) {
@@ -76,19 +75,12 @@ __global__ void __launch_bounds__(NT) gradient_kernel(const uint32_t* __restrict
   const int64_t zlast = (zend < g.nz - 1) ? zend : g.nz - 1;   // vertex slabs [z0, zlast]
 
   // tables into shared memory (dynamic indexing)
-  for (int i = tid; i < 36; i += NT) {
-    sm.tb.triCof[i] = cStar.triCof[i];
-    sm.tb.triEdges[i] = (uint16_t)cStar.triEdges[i];
-    sm.tb.triA[i] = (uint8_t)cStar.triA[i];
-    sm.tb.triB[i] = (uint8_t)cStar.triB[i];
-    sm.tb.cofIdx[i][0] = (uint8_t)cStar.cofIdx[i][0];
-    sm.tb.cofIdx[i][1] = (uint8_t)cStar.cofIdx[i][1];
+  {
+    static_assert(sizeof(lowerstar::Tables) % 4 == 0, "word copy");
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(&cTables);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&sm.tb);
+    for (int i = tid; i < (int)(sizeof(lowerstar::Tables) / 4); i += NT) dst[i] = src[i];
   }
-  for (int i = tid; i < 24; i += NT) {
-    sm.tb.tetFmask[i] = cStar.tetFmask[i];
-    for (int w = 0; w < 3; ++w) sm.tb.tetF[i][w] = (uint8_t)cStar.tetF[i][w];
-  }
-  for (int i = tid; i < 14; i += NT) sm.tb.edgeCof[i] = cStar.edgeCof[i];
   for (int i = tid; i < 2 * TX * TY; i += NT) (&sm.recs[0][0][0])[i] = 0ull;
   if (tid < 4) sm.counts[tid] = 0;
   load_slab(sm, order, g, x0, y0, z0 - 1, (int)((z0 + 2) % 3));

@@ -57,6 +57,20 @@ DMS_HD int popc64(uint64_t m) {
 DMS_HD uint32_t umax(uint32_t a, uint32_t b) { return a > b ? a : b; }
 DMS_HD uint32_t umin(uint32_t a, uint32_t b) { return a < b ? a : b; }
 
+// per-thread keys of the lower-star simplices, stored transposed ([item][thread])
+// so that a warp touches consecutive bytes.  A key lists the ranks (among the
+// lower neighbours of x) of the other vertices by decreasing value, as
+// nibbles h+1, m+1, l+1 (absent ones 0): edges keep an 8-bit (h+1) << 4
+// (the 12-bit key shifted right by 4), tets the 12-bit key, and triangles
+// their rank-pair position h*(h-1)/2 + l, a numbering in which increasing
+// positions are increasing keys.
+template <int NT>
+struct Keys {
+  uint16_t q[24][NT];
+  uint8_t tp[36][NT];  // triangle -> rank-pair position h*(h-1)/2 + l
+  uint8_t e[14][NT];
+};
+
 // the star tables needed with run-time indices
 struct Tables {
   uint64_t edgeCof[14];
@@ -66,6 +80,8 @@ struct Tables {
   uint8_t triA[36], triB[36];
   uint8_t tetF[24][3];
   uint8_t cofIdx[36][2];
+  uint8_t triOfSlots[14][14];  // star triangle on slots (a, b), 255 if none
+  uint8_t hlOfPos[91];         // rank-pair position -> (h << 4) | l
 };
 
 
@@ -74,7 +90,7 @@ struct Tables {
 // acc[c], the record bits contributed to the anchor x - corner c.
 template <int NT>
 DMS_HD int process_lower_star(uint32_t ox, const uint32_t (&o)[14], const Tables& tb,
-                              uint16_t (*keys)[NT], int tid, uint64_t (&acc)[8]) {
+                              Keys<NT>& keys, int tid, uint64_t (&acc)[8]) {
 #pragma unroll
   for (int c = 0; c < 8; ++c) acc[c] = 0;
   uint32_t lm = 0;
@@ -98,13 +114,17 @@ DMS_HD int process_lower_star(uint32_t ox, const uint32_t (&o)[14], const Tables
     }
   }
   auto rank = [&](int s) -> uint32_t { return (uint32_t)(R >> (4 * s)) & 15u; };
+  uint64_t INV = 0;  // slot of each rank, 4 bits per rank
+#pragma unroll
+  for (int s = 0; s < 14; ++s)
+    if ((lm >> s) & 1) INV |= (uint64_t)s << (4 * rank(s));
 
   // the lower star and the keys of its simplices
   uint64_t TL = 0;
   uint32_t QL = 0;
 #pragma unroll
   for (int s = 0; s < 14; ++s)
-    if ((lm >> s) & 1) keys[s][tid] = (uint16_t)((rank(s) + 1) << 8);
+    if ((lm >> s) & 1) keys.e[s][tid] = (uint8_t)((rank(s) + 1) << 4);
   static_for<0, 36>([&](auto J) {
     constexpr int j = decltype(J)::value;
     constexpr int a = kStar.triA[j], b = kStar.triB[j];
@@ -112,7 +132,7 @@ DMS_HD int process_lower_star(uint32_t ox, const uint32_t (&o)[14], const Tables
       TL |= 1ull << j;
       uint32_t ra = rank(a), rb = rank(b);
       uint32_t h = umax(ra, rb), l = umin(ra, rb);
-      keys[14 + j][tid] = (uint16_t)(((h + 1) << 8) | ((l + 1) << 4));
+      keys.tp[j][tid] = (uint8_t)((h * (h - 1)) / 2 + l);
     }
   });
   static_for<0, 24>([&](auto Q) {
@@ -123,82 +143,108 @@ DMS_HD int process_lower_star(uint32_t ox, const uint32_t (&o)[14], const Tables
       uint32_t ra = rank(a), rb = rank(b), rc = rank(c);
       uint32_t h = umax(ra, umax(rb, rc)), l = umin(ra, umin(rb, rc));
       uint32_t m = ra + rb + rc - h - l;
-      keys[50 + q][tid] = (uint16_t)(((h + 1) << 8) | ((m + 1) << 4) | (l + 1));
+      keys.q[q][tid] = (uint16_t)(((h + 1) << 8) | ((m + 1) << 4) | (l + 1));
     }
   });
 
   // ProcessLowerStars (reading of Robins et al.; "classified" = paired or
-  // critical; nuf = unclassified facets inside L)
-  uint32_t cE = 1u << delta;  // x is paired with the edge to delta
-  uint64_t cT = 0;
-  uint32_t cQ = 0;
+  // critical; nuf = number of unclassified facets inside L).
+  //
+  // nuf is tracked bit-parallel: C1/C2 = triangles with >= 1 / 2 classified
+  // edges, Q1/Q2/Q3 = tets with >= 1 / 2 / 3 classified facet triangles, so
+  // "nuf == 1" is C1 & ~C2 (triangles) or Q2 & ~Q3 (tets) and every push of
+  // cofacets is a handful of mask operations.  The two nested loops of the
+  // algorithm (drain PQone, then pop one PQzero element) are one flat loop
+  // whose body pops from PQone when it is non-empty and from PQzero
+  // otherwise -- the same sequence of pops, with less divergence.
+  uint32_t cE = 0;
+  uint64_t cT = 0, C1 = 0, C2 = 0;
+  uint32_t cQ = 0, Q1 = 0, Q2 = 0, Q3 = 0;
+  auto classify_edge = [&](int s) {
+    cE |= 1u << s;
+    const uint64_t M = tb.edgeCof[s];
+    C2 |= C1 & M;
+    C1 |= M;
+  };
+  auto classify_tri = [&](int j) {
+    cT |= 1ull << j;
+    const uint32_t M = tb.triCof[j];
+    Q3 |= Q2 & M;
+    Q2 |= Q1 & M;
+    Q1 |= M;
+  };
+  classify_edge(delta);  // x is paired with the edge to delta
   uint32_t zE = lm & ~cE;  // PQzero
   uint64_t zT = 0;
   uint32_t zQ = 0;
-  uint64_t pT = tb.edgeCof[delta] & TL;  // PQone: their other edge is unclassified
+  // PQone: triangles in rank-pair position space (pop-min = find first set),
+  // mirrored in star numbering (pTj) for membership; tets by key scan
+  uint64_t pP0 = 0, pP1 = 0, pTj = 0;
   uint32_t pQ = 0;
+  auto push_tris = [&](uint64_t nt) {
+    nt &= ~pTj;
+    pTj |= nt;
+    for (; nt; nt &= nt - 1) {
+      const uint32_t p = keys.tp[ffs64(nt)][tid];
+      if (p < 64) pP0 |= 1ull << p;
+      else pP1 |= 1ull << (p - 64);
+    }
+  };
+  auto tri_key = [&](int j) -> uint32_t {
+    const uint32_t hl = tb.hlOfPos[keys.tp[j][tid]];
+    return (((hl >> 4) + 1) << 8) | (((hl & 15u) + 1) << 4);
+  };
+  push_tris(tb.edgeCof[delta] & TL);  // their other edge is unclassified
   uint32_t critE = 0;
   uint64_t critT = 0;
   uint64_t edgeUp = 0;   // 4 bits per edge slot: 1 + cofacet index
   uint64_t tetDown = 0;  // 2 bits per tet: 1 + which L-facet
 
-  // push every unclassified cofacet with exactly one unclassified facet
-  auto push_tri_cofacets_of_edge = [&](int s) {
-    for (uint64_t m = tb.edgeCof[s] & TL & ~cT; m; m &= m - 1) {
-      int t = ffs64(m);
-      if (popc32(~cE & (uint32_t)tb.triEdges[t]) == 1) pT |= 1ull << t;
-    }
-  };
-  auto push_tet_cofacets_of_tri = [&](int j) {
-    for (uint32_t m = tb.triCof[j] & QL & ~cQ; m; m &= m - 1) {
-      int q = ffs32(m);
-      if (popc64(~cT & tb.tetFmask[q]) == 1) pQ |= 1u << q;
-    }
-  };
-
   for (;;) {
-    while (pT | pQ) {
-      uint32_t best = 0xFFFFu;
-      int bi = 0;
-      bool btet = false;
-      for (uint64_t m = pT; m; m &= m - 1) {
-        int j = ffs64(m);
-        uint32_t k = keys[14 + j][tid];
-        if (k < best) { best = k; bi = j; btet = false; }
+    if (pP0 | pP1 | pQ) {
+      uint32_t bestT = 0xFFFFu, hl = 0;
+      int pos = 0;
+      if (pP0 | pP1) {
+        pos = pP0 ? ffs64(pP0) : 64 + ffs64(pP1);
+        hl = tb.hlOfPos[pos];
+        bestT = (((hl >> 4) + 1) << 8) | (((hl & 15u) + 1) << 4);
       }
+      uint32_t bestQ = 0xFFFFu;
+      int qb = 0;
       for (uint32_t m = pQ; m; m &= m - 1) {
         int q = ffs32(m);
-        uint32_t k = keys[50 + q][tid];
-        if (k < best) { best = k; bi = q; btet = true; }
+        uint32_t k = keys.q[q][tid];
+        if (k < bestQ) { bestQ = k; qb = q; }
       }
-      if (!btet) {
-        const int j = bi;
-        pT &= ~(1ull << j);
+      if (bestT < bestQ) {
+        if (pos < 64) pP0 &= ~(1ull << pos);
+        else pP1 &= ~(1ull << (pos - 64));
+        const int j = tb.triOfSlots[(INV >> (4 * (hl >> 4))) & 15u][(INV >> (4 * (hl & 15u))) & 15u];
+        pTj &= ~(1ull << j);
         if ((cT >> j) & 1) continue;
-        uint32_t u = ~cE & (uint32_t)tb.triEdges[j];
-        if (u == 0) { zT |= 1ull << j; continue; }
-        const int beta = ffs32(u);
+        if ((C2 >> j) & 1) { zT |= 1ull << j; continue; }  // nuf == 0
+        const int beta = ffs32(~cE & (uint32_t)tb.triEdges[j]);
         const int w = beta == tb.triA[j] ? 0 : 1;
-        cE |= 1u << beta;
-        cT |= 1ull << j;
-        zE &= ~(1u << beta);
         edgeUp |= (uint64_t)(tb.cofIdx[j][w] + 1) << (4 * beta);
-        push_tet_cofacets_of_tri(j);
-        push_tri_cofacets_of_edge(beta);
+        classify_edge(beta);
+        classify_tri(j);
+        zE &= ~(1u << beta);
+        pQ |= tb.triCof[j] & QL & Q2 & ~Q3 & ~cQ;
+        push_tris(tb.edgeCof[beta] & TL & C1 & ~C2 & ~cT);
       } else {
-        const int q = bi;
+        const int q = qb;
         pQ &= ~(1u << q);
         if ((cQ >> q) & 1) continue;
-        uint64_t u = ~cT & tb.tetFmask[q];
-        if (u == 0) { zQ |= 1u << q; continue; }
-        const int beta = ffs64(u);
+        if ((Q3 >> q) & 1) { zQ |= 1u << q; continue; }  // nuf == 0
+        const int beta = ffs64(~cT & tb.tetFmask[q]);
         const int w = beta == tb.tetF[q][0] ? 0 : (beta == tb.tetF[q][1] ? 1 : 2);
-        cT |= 1ull << beta;
+        tetDown |= (uint64_t)(w + 1) << (2 * q);
+        classify_tri(beta);
         cQ |= 1u << q;
         zT &= ~(1ull << beta);
-        tetDown |= (uint64_t)(w + 1) << (2 * q);
-        push_tet_cofacets_of_tri(beta);
+        pQ |= tb.triCof[beta] & QL & Q2 & ~Q3 & ~cQ;
       }
+      continue;
     }
     if (!(zE | zT | zQ)) break;
     // pop-min of PQzero: the next critical simplex
@@ -206,29 +252,29 @@ DMS_HD int process_lower_star(uint32_t ox, const uint32_t (&o)[14], const Tables
     int bi = 0, bd = 0;
     for (uint32_t m = zE; m; m &= m - 1) {
       int s = ffs32(m);
-      uint32_t k = keys[s][tid];
+      uint32_t k = (uint32_t)keys.e[s][tid] << 4;
       if (k < best) { best = k; bi = s; bd = 1; }
     }
     for (uint64_t m = zT; m; m &= m - 1) {
       int j = ffs64(m);
-      uint32_t k = keys[14 + j][tid];
+      uint32_t k = tri_key(j);
       if (k < best) { best = k; bi = j; bd = 2; }
     }
     for (uint32_t m = zQ; m; m &= m - 1) {
       int q = ffs32(m);
-      uint32_t k = keys[50 + q][tid];
+      uint32_t k = keys.q[q][tid];
       if (k < best) { best = k; bi = q; bd = 3; }
     }
     if (bd == 1) {
       zE &= ~(1u << bi);
-      cE |= 1u << bi;
       critE |= 1u << bi;
-      push_tri_cofacets_of_edge(bi);
+      classify_edge(bi);
+      push_tris(tb.edgeCof[bi] & TL & C1 & ~C2 & ~cT);
     } else if (bd == 2) {
       zT &= ~(1ull << bi);
-      cT |= 1ull << bi;
       critT |= 1ull << bi;
-      push_tet_cofacets_of_tri(bi);
+      classify_tri(bi);
+      pQ |= tb.triCof[bi] & QL & Q2 & ~Q3 & ~cQ;
     } else {
       zQ &= ~(1u << bi);
       cQ |= 1u << bi;
@@ -266,7 +312,7 @@ DMS_HD int process_lower_star(uint32_t ox, const uint32_t (&o)[14], const Tables
 }
 
 
-inline Tables make_tables() {
+constexpr Tables make_tables() {
   Tables t{};
   for (int i = 0; i < 14; ++i) t.edgeCof[i] = kStar.edgeCof[i];
   for (int i = 0; i < 24; ++i) {
@@ -281,6 +327,14 @@ inline Tables make_tables() {
     t.cofIdx[i][0] = (uint8_t)kStar.cofIdx[i][0];
     t.cofIdx[i][1] = (uint8_t)kStar.cofIdx[i][1];
   }
+  for (int a = 0; a < 14; ++a)
+    for (int b = 0; b < 14; ++b) t.triOfSlots[a][b] = 255;
+  for (int i = 0; i < 36; ++i) {
+    t.triOfSlots[kStar.triA[i]][kStar.triB[i]] = (uint8_t)i;
+    t.triOfSlots[kStar.triB[i]][kStar.triA[i]] = (uint8_t)i;
+  }
+  for (int h = 1; h < 14; ++h)
+    for (int l = 0; l < h; ++l) t.hlOfPos[h * (h - 1) / 2 + l] = (uint8_t)((h << 4) | l);
   return t;
 }
 

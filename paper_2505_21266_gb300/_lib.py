@@ -19,7 +19,7 @@ class dms_dims(ctypes.Structure):
 
 STATUS = {0: "DMS_OK", 1: "DMS_ERR_NULL", 2: "DMS_ERR_DIMS", 3: "DMS_ERR_NAN",
           4: "DMS_ERR_CAPACITY", 5: "DMS_ERR_WORKSPACE", 6: "DMS_ERR_CUDA",
-          7: "DMS_ERR_TIMEOUT", 8: "DMS_ERR_ARG"}
+          7: "DMS_ERR_TIMEOUT", 8: "DMS_ERR_ARG", 9: "DMS_ERR_TOO_LARGE"}
 
 # (name, restype, argtypes) for every entry point declared in include/dms.h
 _VP, _I64, _I32, _SZ = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_size_t
@@ -33,6 +33,9 @@ SIGNATURES = [
     ("dms_critical_workspace_size", _SZ, [dms_dims]),
     ("dms_critical", ctypes.c_int,
      [_VP, _VP, dms_dims, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP, _VP]),
+    ("dms_critical_noalloc_max_vertices", _I64, []),
+    ("dms_critical_noalloc", ctypes.c_int,
+     [_VP, _VP, dms_dims, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     ("dms_diagram_workspace_size", _SZ, [dms_dims, _VP]),
     ("dms_diagram_d0d2", ctypes.c_int,
      [_VP, _VP, _VP, _VP, dms_dims, _VP, _VP, _VP, _VP, _VP, _VP, _I64, _VP, _I64, _VP, _VP,

@@ -41,6 +41,7 @@ const char* dms_status_string(int status) {
     case DMS_ERR_CUDA: return "a CUDA call failed";
     case DMS_ERR_TIMEOUT: return "an iterative stage hit its iteration limit";
     case DMS_ERR_ARG: return "invalid argument";
+    case DMS_ERR_TOO_LARGE: return "grid larger than the fixed scratch of a no-alloc entry point";
   }
   return "unknown status";
 }

@@ -65,6 +65,14 @@ typedef struct dms_pair {
   uint32_t death_vtx;
 } dms_pair;
 
+/* A field of a batch: its vertices occupy [offset, offset + nx*ny*nz) of the
+ * concatenated per-vertex arrays (fields adjacent, offsets increasing from 0). */
+typedef struct dms_field_desc {
+  int64_t offset;
+  int32_t nx, ny, nz; /* each >= 2, x fastest */
+  int32_t reserved;   /* 0 */
+} dms_field_desc;
+
 typedef enum dms_status {
   DMS_OK = 0,
   DMS_ERR_NULL = 1,       /* a required pointer is NULL */
@@ -204,6 +212,62 @@ int dms_diagram_d0d2(const float* f, const uint32_t* order, const uint8_t* desc,
                      const int64_t* n_crit, dms_pair* d0, int64_t cap0, dms_pair* d2,
                      int64_t cap2, dms_pair* d0_essential, int64_t* n_out, void* ws,
                      size_t ws_bytes, int32_t* dstatus, void* stream);
+
+/* ---------------------------------------------------------------- batch ---
+ * dms_batch_diagrams -- (i)-(iv) for many fields of uneven dims at once
+ * (the batch processing the paper contrasts with its per-dataset runs,
+ * Sec. 2.6): one segmented order sort, one persistent gradient kernel whose
+ * CTAs take tiles of all fields from a shared queue, one compaction, one set
+ * of pairing rounds over the disjoint union of the fields' extremum graphs.
+ * Nothing synchronises the host, so the whole call can be captured in a CUDA
+ * graph and replayed.
+ *   f            concatenated float32 fields (sum of the fields' sizes).
+ *   fields_host  [nfields] table (host), fields_dev the same table on the
+ *                device (both read during the call).
+ *   tile_variant gradient tile shape, 0..dms_batch_tile_variants()-1 (32 x 24,
+ *                32 x 16, 32 x 32 anchors per CTA; an autotuner picks one).
+ *   order, desc, rec  concatenated outputs as in dms_order/dms_gradient, each
+ *                field with its own local order and records.
+ *   caps         host [4]: capacity, over all fields, of the critical lists
+ *                (kept in the workspace); cap_pairs: capacity of d0 and of d2.
+ *   d0, d2       pairs with ids and vertex indices LOCAL to their field, in
+ *                field order (then saddle-id order); pair_offsets [2][nfields+1]
+ *                (device) delimit each field's pairs; d0_essential [nfields].
+ *   counts       device [6]: critical simplices per dimension, then the
+ *                numbers of D0 and D2 pairs (a count above its capacity sets
+ *                (1 << DMS_ERR_CAPACITY); the call can then be repeated with
+ *                larger capacities).
+ *   ws           at least dms_batch_workspace_size(...) bytes.
+ * The pairing runs at most dms_batch_max_rounds() rounds and then finishes at
+ * most 4096 saddles in order; beyond that (1 << DMS_ERR_TIMEOUT) is set and
+ * the per-field entry points should be used.
+ */
+int32_t dms_batch_tile_variants(void);
+int32_t dms_batch_max_rounds(void);
+size_t dms_batch_workspace_size(const dms_field_desc* fields_host, int32_t nfields,
+                                const int64_t* caps, int64_t cap_pairs);
+int dms_batch_diagrams(const float* f, const dms_field_desc* fields_host,
+                       const dms_field_desc* fields_dev, int32_t nfields, int32_t tile_variant,
+                       uint32_t* order, uint8_t* desc, uint64_t* rec, const int64_t* caps,
+                       int64_t cap_pairs, dms_pair* d0, dms_pair* d2, int64_t* pair_offsets,
+                       dms_pair* d0_essential, int64_t* counts, void* ws, size_t ws_bytes,
+                       int32_t* dstatus, void* stream);
+
+/* ------------------------------------------------------------------ diff ---
+ * dms_backward -- gradient of a loss on diagram values with respect to the
+ * field.  A pair sits at (f(birth simplex), f(death simplex)), f(s) being the
+ * value of the highest vertex of s (Sec. 2.4); the pairing depends on the
+ * order of the values only, so it is locally constant and
+ *   dL/df[v] = sum_i g[i][0] [birth_vtx_i == v] + g[i][1] [death_vtx_i == v].
+ *   pairs  [n] dms_pair from dms_diagram_d0d2 (D0, D2 or the essential class;
+ *          a pair with death_id < 0 contributes its birth term only).
+ *   g      [n][2] float32: dL/dbirth, dL/ddeath of each pair.
+ *   grad   [N] float32, ACCUMULATED into (zero it first).  Pairs sharing a
+ *          carrier vertex are added with float atomics in no fixed order.
+ * A carrier outside the grid sets (1 << DMS_ERR_ARG) in *dstatus.
+ */
+int dms_backward(const dms_pair* pairs, int64_t n, const float* g, dms_dims d, float* grad,
+                 int32_t* dstatus, void* stream);
 
 #ifdef __cplusplus
 }

@@ -17,6 +17,11 @@ class dms_dims(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32)]
 
 
+class dms_field_desc(ctypes.Structure):
+    _fields_ = [("offset", ctypes.c_int64), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("nz", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 STATUS = {0: "DMS_OK", 1: "DMS_ERR_NULL", 2: "DMS_ERR_DIMS", 3: "DMS_ERR_NAN",
           4: "DMS_ERR_CAPACITY", 5: "DMS_ERR_WORKSPACE", 6: "DMS_ERR_CUDA",
           7: "DMS_ERR_TIMEOUT", 8: "DMS_ERR_ARG", 9: "DMS_ERR_TOO_LARGE"}
@@ -36,10 +41,17 @@ SIGNATURES = [
     ("dms_critical_noalloc_max_vertices", _I64, []),
     ("dms_critical_noalloc", ctypes.c_int,
      [_VP, _VP, dms_dims, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
+    ("dms_backward", ctypes.c_int, [_VP, _I64, _VP, dms_dims, _VP, _VP, _VP]),
     ("dms_diagram_workspace_size", _SZ, [dms_dims, _VP]),
     ("dms_diagram_d0d2", ctypes.c_int,
      [_VP, _VP, _VP, _VP, dms_dims, _VP, _VP, _VP, _VP, _VP, _VP, _I64, _VP, _I64, _VP, _VP,
       _VP, _SZ, _VP, _VP]),
+    ("dms_batch_tile_variants", _I32, []),
+    ("dms_batch_max_rounds", _I32, []),
+    ("dms_batch_workspace_size", _SZ, [_VP, _I32, _VP, _I64]),
+    ("dms_batch_diagrams", ctypes.c_int,
+     [_VP, _VP, _VP, _I32, _I32, _VP, _VP, _VP, _VP, _I64, _VP, _VP, _VP, _VP, _VP, _VP, _SZ,
+      _VP, _VP]),
 ]
 
 

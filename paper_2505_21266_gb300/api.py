@@ -197,3 +197,65 @@ def diagram_from_host(field_host, device="cuda"):
     res = diagram(f)
     return (res.diagrams.numpy("d0"), res.diagrams.numpy("d2"),
             res.diagrams.numpy("d0_essential"))
+
+
+# ------------------------------------------------------------------ diff --
+
+def pair_values(pairs: torch.Tensor) -> torch.Tensor:
+    """(birth, death) float32 values [n, 2] of pair records [n, 32]."""
+    return pairs.view(torch.float32).reshape(-1, PAIR_BYTES // 4)[:, 4:6]
+
+
+def backward(pairs: torch.Tensor, g: torch.Tensor, grad: torch.Tensor,
+             status: torch.Tensor | None = None):
+    """grad[carrier] += dL/d(value) for every pair (dms_backward)."""
+    lib = _lib.load()
+    g = g.to(torch.float32).contiguous()
+    n = int(pairs.shape[0]) if pairs.numel() else 0
+    if n == 0:
+        return grad
+    st = status if status is not None else torch.zeros(1, dtype=torch.int32, device=grad.device)
+    _check(lib.dms_backward(_ptr(pairs), n, _ptr(g), dims_of(grad), _ptr(grad), _ptr(st),
+                            _stream(grad.device)), "dms_backward")
+    if status is None:
+        _device_status_check(st, "dms_backward")
+    return grad
+
+
+class DiagramFn(torch.autograd.Function):
+    """Differentiable D0/D2 diagrams: forward returns the (birth, death) values
+    of the D0 and D2 pairs; backward scatter-adds the incoming gradients onto
+    the carrier vertices with the dms_backward kernel."""
+
+    @staticmethod
+    def forward(ctx, field):
+        res = diagram(field.detach().contiguous())
+        d0, d2 = res.diagrams.d0, res.diagrams.d2
+        ctx.save_for_backward(d0, d2)
+        ctx.field_shape = field.shape
+        return pair_values(d0).clone(), pair_values(d2).clone()
+
+    @staticmethod
+    def backward(ctx, g0, g2):
+        d0, d2 = ctx.saved_tensors
+        grad = torch.zeros(ctx.field_shape, dtype=torch.float32, device=d0.device)
+        if g0 is not None and d0.shape[0]:
+            backward(d0, g0, grad)
+        if g2 is not None and d2.shape[0]:
+            backward(d2, g2, grad)
+        return grad
+
+
+def diagram_values(field: torch.Tensor):
+    """Autograd entry point: (D0 values [n0, 2], D2 values [n2, 2])."""
+    return DiagramFn.apply(field)
+
+
+def topological_loss(field: torch.Tensor, threshold: float = 0.05) -> torch.Tensor:
+    """Sum over the D0 and D2 pairs with persistence below `threshold` of
+    (death - birth)^2 -- a topological simplification loss."""
+    v0, v2 = diagram_values(field)
+    v = torch.cat([v0, v2])
+    pers = v[:, 1] - v[:, 0]
+    keep = pers < threshold
+    return (pers[keep] ** 2).sum()

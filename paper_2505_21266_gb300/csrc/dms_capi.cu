@@ -20,6 +20,8 @@ int launch_diagram(const float* f, const uint32_t* order, const uint8_t* desc, c
                    const int64_t* crit3, const int64_t* nc, dms_pair* d0, int64_t cap0,
                    dms_pair* d2, int64_t cap2, dms_pair* ess, int64_t* n_out, void* ws,
                    int32_t* dstatus, cudaStream_t s);
+int launch_backward(const dms_pair* pairs, int64_t n, const float* g, const Grid& grid,
+                    float* grad, int32_t* dstatus, cudaStream_t s);
 long long& launch_counter() {
   static long long n = 0;
   return n;
@@ -123,6 +125,16 @@ int dms_diagram_d0d2(const float* f, const uint32_t* order, const uint8_t* desc,
   return dms::launch_diagram(f, order, desc, rec, g, crit0, crit1, crit2, crit3, n_crit, d0, cap0,
                              d2, cap2, d0_essential, n_out, ws, dstatus,
                              static_cast<cudaStream_t>(stream));
+}
+
+int dms_backward(const dms_pair* pairs, int64_t n, const float* g, dms_dims d, float* grad,
+                 int32_t* dstatus, void* stream) {
+  Grid gr;
+  if (!dms::make_grid(d, &gr)) return DMS_ERR_DIMS;
+  if (n < 0) return DMS_ERR_ARG;
+  if (n > 0 && (!pairs || !g)) return DMS_ERR_NULL;
+  if (!grad || !dstatus) return DMS_ERR_NULL;
+  return dms::launch_backward(pairs, n, g, gr, grad, dstatus, static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

@@ -38,8 +38,7 @@
 namespace dms {
 namespace {
 
-constexpr int TX = 32, TY = 24;
-constexpr int WX = TX + 3, WY = TY + 3;
+constexpr int TX = 32;
 constexpr int NT = 256;
 
 __constant__ lowerstar::Tables cTables = lowerstar::make_tables();
@@ -50,20 +49,26 @@ constexpr uint64_t kEdgeLsb = 0x49249ull;      // bits 0,3,..,18
 constexpr uint64_t kTriMask = 0xFFFull << 21;  // bits 21..32
 constexpr uint64_t kTetLsb = 0x9249ull << 33;  // bits 33,36,..,48
 
+// shared memory of a CTA working on tiles of TX x TY anchors
+template <int TY>
 struct Smem {
+  static constexpr int WX = TX + 3, WY = TY + 3;
   lowerstar::Tables tb;
   uint32_t win[3][WY][WX];
   unsigned long long recs[2][TY][TX];
   lowerstar::Keys<NT> keys;
-  uint16_t perm[(TX + 1) * (TY + 1)];  // slab vertices grouped by lower-neighbour count
+  uint16_t perm[(TX + 1) * (TY + 1)];  // slab vertices grouped by lower-star size
   uint8_t kcnt[(TX + 1) * (TY + 1)];
   unsigned int bucket[64];
   unsigned int next_task;
   unsigned int counts[4];
+  long long tile;  // batched kernel: the tile this CTA works on
 };
 
-__device__ __forceinline__ void load_slab(Smem& sm, const uint32_t* __restrict__ order,
+template <int TY>
+__device__ __forceinline__ void load_slab(Smem<TY>& sm, const uint32_t* __restrict__ order,
                                           const Grid& g, int x0, int y0, int64_t zs, int slot) {
+  constexpr int WX = Smem<TY>::WX, WY = Smem<TY>::WY;
   for (int i = threadIdx.x; i < WX * WY; i += NT) {
     int wx = i % WX, wy = i / WX;
     int64_t gx = x0 - 1 + wx, gy = y0 - 1 + wy;
@@ -74,31 +79,29 @@ __device__ __forceinline__ void load_slab(Smem& sm, const uint32_t* __restrict__
   }
 }
 
-__global__ void __launch_bounds__(NT, 4) gradient_kernel(const uint32_t* __restrict__ order, Grid g,
-                                                      int zc, uint8_t* __restrict__ desc,
-                                                      uint64_t* __restrict__ rec,
-                                                      unsigned long long* __restrict__ counts) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const int64_t z0 = (int64_t)blockIdx.z * zc;
-  const int64_t zend = (z0 + zc < g.nz) ? z0 + zc : g.nz;     // anchor slabs [z0, zend)
-  const int64_t zlast = (zend < g.nz - 1) ? zend : g.nz - 1;   // vertex slabs [z0, zlast]
+template <int TY>
+__device__ __forceinline__ void load_tables(Smem<TY>& sm) {
+  static_assert(sizeof(lowerstar::Tables) % 4 == 0, "word copy");
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(&cTables);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(&sm.tb);
+  for (int i = threadIdx.x; i < (int)(sizeof(lowerstar::Tables) / 4); i += NT) dst[i] = src[i];
+}
 
-  // tables into shared memory (dynamic indexing)
-  {
-    static_assert(sizeof(lowerstar::Tables) % 4 == 0, "word copy");
-    const uint32_t* src = reinterpret_cast<const uint32_t*>(&cTables);
-    uint32_t* dst = reinterpret_cast<uint32_t*>(&sm.tb);
-    for (int i = tid; i < (int)(sizeof(lowerstar::Tables) / 4); i += NT) dst[i] = src[i];
-  }
-  for (int i = tid; i < 2 * TX * TY; i += NT) (&sm.recs[0][0][0])[i] = 0ull;
-  if (tid < 4) sm.counts[tid] = 0;
+// The anchors [x0, x0+TX) x [y0, y0+TY) x [z0, zend) of one field: computes
+// the lower stars of the vertices [x0, x0+TX] x [y0, y0+TY] x [z0, zend]
+// (the +1 halo) slab by slab and writes complete records and desc.  Adds the
+// critical simplices of the written records to ncrit (per thread) and the
+// minima to sm.counts[0].  Requires sm.tb loaded, sm.recs zero.
+template <int TY>
+__device__ void gradient_tile(Smem<TY>& sm, const uint32_t* __restrict__ order, const Grid& g,
+                              int x0, int y0, int64_t z0, int64_t zend, uint8_t* __restrict__ desc,
+                              uint64_t* __restrict__ rec, unsigned int (&ncrit)[3]) {
+  constexpr int WX = Smem<TY>::WX;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t zlast = (zend < g.nz - 1) ? zend : g.nz - 1;  // vertex slabs [z0, zlast]
   load_slab(sm, order, g, x0, y0, z0 - 1, (int)((z0 + 2) % 3));
   load_slab(sm, order, g, x0, y0, z0, (int)(z0 % 3));
 
-  unsigned int ncrit[3] = {0, 0, 0};  // critical edges, triangles, tets flushed by this thread
   const int nvx = TX + 1, nvy = TY + 1;
   const int ntask = (nvx * nvy + 31) / 32;
   for (int64_t z = z0; z <= zlast; ++z) {
@@ -108,8 +111,8 @@ __global__ void __launch_bounds__(NT, 4) gradient_kernel(const uint32_t* __restr
     const Row* wm = sm.win[(z + 2) % 3];
     const Row* w0 = sm.win[z % 3];
     const Row* wp = sm.win[(z + 1) % 3];
-    // group the slab's vertices by their number of lower neighbours so that
-    // the lanes of a warp get lower stars of similar size (less divergence)
+    // group the slab's vertices by the size of their lower star so that the
+    // lanes of a warp get similar work; warps take groups largest-first
     if (tid < 64) sm.bucket[tid] = 0;
     __syncthreads();
     for (int i = tid; i < nvx * nvy; i += NT) {
@@ -154,30 +157,30 @@ __global__ void __launch_bounds__(NT, 4) gradient_kernel(const uint32_t* __restr
       const int lx = idx % nvx, ly = idx / nvx;
       const int64_t x = x0 + lx, y = y0 + ly;
       if (slot < nvx * nvy && x < g.nx && y < g.ny) {
-      const int cx = lx + 1, cy = ly + 1;
-      uint32_t o[14];
-      static_for<0, 14>([&](auto S) {
-        constexpr int s = decltype(S)::value;
-        constexpr int dx = kStar.off[s][0], dy = kStar.off[s][1], dz = kStar.off[s][2];
-        const Row* w = dz < 0 ? wm : (dz > 0 ? wp : w0);
-        o[s] = w[cy + dy][cx + dx];
-      });
-      const uint32_t ox = w0[cy][cx];
-      uint64_t acc[8];
-      int d = lowerstar::process_lower_star<NT>(ox, o, sm.tb, sm.keys, tid, acc);
-      const bool owned = lx < TX && ly < TY && z < zend;
-      if (owned) {
-        desc[x + g.nx * (y + g.ny * z)] = (uint8_t)d;
-        if (d == 15) atomicAdd(&sm.counts[0], 1u);
-      }
+        const int cx = lx + 1, cy = ly + 1;
+        uint32_t o[14];
+        static_for<0, 14>([&](auto S) {
+          constexpr int s = decltype(S)::value;
+          constexpr int dx = kStar.off[s][0], dy = kStar.off[s][1], dz = kStar.off[s][2];
+          const Row* w = dz < 0 ? wm : (dz > 0 ? wp : w0);
+          o[s] = w[cy + dy][cx + dx];
+        });
+        const uint32_t ox = w0[cy][cx];
+        uint64_t acc[8];
+        int d = lowerstar::process_lower_star<NT>(ox, o, sm.tb, sm.keys, tid, acc);
+        const bool owned = lx < TX && ly < TY && z < zend;
+        if (owned) {
+          desc[x + g.nx * (y + g.ny * z)] = (uint8_t)d;
+          if (d == 15) atomicAdd(&sm.counts[0], 1u);
+        }
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        if (!acc[c]) continue;
-        const int ax = lx - (c & 1), ay = ly - ((c >> 1) & 1);
-        const int64_t az = z - ((c >> 2) & 1);
-        if (ax < 0 || ax >= TX || ay < 0 || ay >= TY || az < z0 || az >= zend) continue;
-        atomicOr(&sm.recs[az & 1][ay][ax], (unsigned long long)acc[c]);
-      }
+        for (int c = 0; c < 8; ++c) {
+          if (!acc[c]) continue;
+          const int ax = lx - (c & 1), ay = ly - ((c >> 1) & 1);
+          const int64_t az = z - ((c >> 2) & 1);
+          if (ax < 0 || ax >= TX || ay < 0 || ay >= TY || az < z0 || az >= zend) continue;
+          atomicOr(&sm.recs[az & 1][ay][ax], (unsigned long long)acc[c]);
+        }
       }
       unsigned int nt = 0;
       if (lane == 0) nt = atomicAdd(&sm.next_task, 1u);
@@ -207,23 +210,122 @@ __global__ void __launch_bounds__(NT, 4) gradient_kernel(const uint32_t* __restr
     }
     __syncthreads();
   }
+}
+
+// adds the CTA's critical counts to counts[4] (all threads must call)
+template <int TY>
+__device__ __forceinline__ void add_counts(Smem<TY>& sm, unsigned int (&ncrit)[3],
+                                           unsigned long long* counts) {
+  const int tid = threadIdx.x, lane = tid & 31;
   for (int d = 0; d < 3; ++d) {
     unsigned int v = ncrit[d];
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
     if (lane == 0 && v) atomicAdd(&sm.counts[d + 1], v);
+    ncrit[d] = 0;
   }
   __syncthreads();
-  if (tid < 4 && sm.counts[tid]) atomicAdd(&counts[tid], (unsigned long long)sm.counts[tid]);
+  if (tid < 4) {
+    if (sm.counts[tid]) atomicAdd(&counts[tid], (unsigned long long)sm.counts[tid]);
+    sm.counts[tid] = 0;
+  }
+  __syncthreads();
 }
 
-}  // namespace
+// one field, one CTA per tile of anchors
+template <int TY>
+__global__ void __launch_bounds__(NT, 4) gradient_kernel(const uint32_t* __restrict__ order, Grid g,
+                                                      int zc, uint8_t* __restrict__ desc,
+                                                      uint64_t* __restrict__ rec,
+                                                      unsigned long long* __restrict__ counts) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem<TY>& sm = *reinterpret_cast<Smem<TY>*>(smem_raw);
+  const int tid = threadIdx.x;
+  load_tables(sm);
+  for (int i = tid; i < 2 * TX * TY; i += NT) (&sm.recs[0][0][0])[i] = 0ull;
+  if (tid < 4) sm.counts[tid] = 0;
+  const int64_t z0 = (int64_t)blockIdx.z * zc;
+  const int64_t zend = (z0 + zc < g.nz) ? z0 + zc : g.nz;
+  unsigned int ncrit[3] = {0, 0, 0};
+  gradient_tile(sm, order, g, blockIdx.x * TX, blockIdx.y * TY, z0, zend, desc, rec, ncrit);
+  add_counts(sm, ncrit, counts);
+}
 
-int launch_gradient(const uint32_t* order, const Grid& g, uint8_t* desc, uint64_t* rec,
-                    int64_t* crit_counts, cudaStream_t s) {
+// Many fields, persistent: every CTA takes tiles from one queue that runs over
+// all fields (field f owns tiles [tile0[f], tile0[f+1])), so uneven fields
+// share the GPU without one launch per field.
+struct BatchTiles {
+  const dms_field_desc* fields;
+  const long long* tile0;  // nfields + 1 prefix counts of tiles
+  int nfields;
+  int zc;                  // anchor slabs per tile
+  unsigned long long* queue;
+};
+
+template <int TY>
+__global__ void __launch_bounds__(NT, 4) gradient_batch_kernel(const uint32_t* __restrict__ order,
+                                                            BatchTiles bt,
+                                                            uint8_t* __restrict__ desc,
+                                                            uint64_t* __restrict__ rec,
+                                                            unsigned long long* __restrict__ counts) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem<TY>& sm = *reinterpret_cast<Smem<TY>*>(smem_raw);
+  const int tid = threadIdx.x;
+  load_tables(sm);
+  for (int i = tid; i < 2 * TX * TY; i += NT) (&sm.recs[0][0][0])[i] = 0ull;
+  if (tid < 4) sm.counts[tid] = 0;
+  const long long total = bt.tile0[bt.nfields];
+  unsigned int ncrit[3] = {0, 0, 0};
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) sm.tile = (long long)atomicAdd(bt.queue, 1ull);
+    __syncthreads();
+    const long long t = sm.tile;
+    if (t >= total) break;
+    int lo = 0, hi = bt.nfields;  // the field holding tile t
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (bt.tile0[mid] <= t) lo = mid;
+      else hi = mid;
+    }
+    const dms_field_desc fd = bt.fields[lo];
+    Grid g;
+    g.nx = fd.nx;
+    g.ny = fd.ny;
+    g.nz = fd.nz;
+    g.sxy = (int64_t)fd.nx * fd.ny;
+    g.n = g.sxy * fd.nz;
+    const long long local = t - bt.tile0[lo];
+    const int tx = (fd.nx + TX - 1) / TX, ty = (fd.ny + TY - 1) / TY;
+    const long long bx = local % tx, by = (local / tx) % ty, bz = local / ((long long)tx * ty);
+    const int64_t z0 = bz * bt.zc;
+    const int64_t zend = (z0 + bt.zc < g.nz) ? z0 + bt.zc : g.nz;
+    gradient_tile(sm, order + fd.offset, g, (int)bx * TX, (int)by * TY, z0, zend,
+                  desc + fd.offset, rec + fd.offset, ncrit);
+    add_counts(sm, ncrit, counts + 4 * lo);
+  }
+}
+
+// tile counts per field -> prefix (one small CTA)
+__global__ void batch_tiles_kernel(const dms_field_desc* __restrict__ fields, int nfields, int ty,
+                                   int zc, long long* tile0, unsigned long long* queue) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  long long acc = 0;
+  for (int f = 0; f < nfields; ++f) {
+    tile0[f] = acc;
+    const dms_field_desc fd = fields[f];
+    acc += (long long)((fd.nx + TX - 1) / TX) * ((fd.ny + ty - 1) / ty) * ((fd.nz + zc - 1) / zc);
+  }
+  tile0[nfields] = acc;
+  *queue = 0ull;
+}
+
+template <int TY>
+int launch_single(const uint32_t* order, const Grid& g, uint8_t* desc, uint64_t* rec,
+                  int64_t* crit_counts, cudaStream_t s) {
   static bool configured = false;
-  const size_t smem = sizeof(Smem);
+  const size_t smem = sizeof(Smem<TY>);
   if (!configured) {
-    if (cudaFuncSetAttribute(gradient_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(gradient_kernel<TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
       return DMS_ERR_CUDA;
     configured = true;
@@ -240,9 +342,57 @@ int launch_gradient(const uint32_t* order, const Grid& g, uint8_t* desc, uint64_
   nzc = (g.nz + zc - 1) / zc;
   if (cudaMemsetAsync(crit_counts, 0, 4 * sizeof(int64_t), s) != cudaSuccess) return DMS_ERR_CUDA;
   dim3 grid((unsigned)tx, (unsigned)ty, (unsigned)nzc);
-  gradient_kernel<<<grid, NT, smem, s>>>(order, g, zc, desc, rec,
-                                         reinterpret_cast<unsigned long long*>(crit_counts)); count_launch();
+  gradient_kernel<TY><<<grid, NT, smem, s>>>(order, g, zc, desc, rec,
+                                             reinterpret_cast<unsigned long long*>(crit_counts)); count_launch();
   return launch_status();
+}
+
+template <int TY>
+int launch_batch(const uint32_t* order, const dms_field_desc* fields_dev, int nfields, int zc,
+                 uint8_t* desc, uint64_t* rec, int64_t* counts, long long* tile0,
+                 unsigned long long* queue, cudaStream_t s) {
+  static bool configured = false;
+  const size_t smem = sizeof(Smem<TY>);
+  if (!configured) {
+    if (cudaFuncSetAttribute(gradient_batch_kernel<TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return DMS_ERR_CUDA;
+    configured = true;
+  }
+  int dev = 0, sms = 148, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gradient_batch_kernel<TY>, NT, smem) !=
+          cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  DMS_CUDA_OK(cudaMemsetAsync(counts, 0, 4 * sizeof(int64_t) * nfields, s));
+  batch_tiles_kernel<<<1, 32, 0, s>>>(fields_dev, nfields, TY, zc, tile0, queue); count_launch();
+  BatchTiles bt{fields_dev, tile0, nfields, zc, queue};
+  gradient_batch_kernel<TY><<<(unsigned)(sms * per_sm), NT, smem, s>>>(
+      order, bt, desc, rec, reinterpret_cast<unsigned long long*>(counts)); count_launch();
+  return launch_status();
+}
+
+}  // namespace
+
+// tile heights compiled for the autotuner (index = variant)
+constexpr int kTileVariants = 3;
+int gradient_tile_height(int variant) { return variant == 1 ? 16 : (variant == 2 ? 32 : 24); }
+
+int launch_gradient(const uint32_t* order, const Grid& g, uint8_t* desc, uint64_t* rec,
+                    int64_t* crit_counts, cudaStream_t s) {
+  return launch_single<24>(order, g, desc, rec, crit_counts, s);
+}
+
+int launch_gradient_batch(const uint32_t* order, const dms_field_desc* fields_dev, int nfields,
+                          int variant, int zc, uint8_t* desc, uint64_t* rec, int64_t* counts,
+                          long long* tile0, unsigned long long* queue, cudaStream_t s) {
+  switch (variant) {
+    case 1: return launch_batch<16>(order, fields_dev, nfields, zc, desc, rec, counts, tile0, queue, s);
+    case 2: return launch_batch<32>(order, fields_dev, nfields, zc, desc, rec, counts, tile0, queue, s);
+    default: return launch_batch<24>(order, fields_dev, nfields, zc, desc, rec, counts, tile0, queue, s);
+  }
 }
 
 }  // namespace dms

@@ -22,9 +22,9 @@
 namespace dms {
 namespace {
 
-constexpr int SORT_NT = 512;
+constexpr int SORT_NT = 256;
 constexpr int SORT_ITEMS = 16;
-constexpr int SORT_TILE = SORT_NT * SORT_ITEMS;  // 8192
+constexpr int SORT_TILE = SORT_NT * SORT_ITEMS;  // 4096
 constexpr int SORT_WARPS = SORT_NT / 32;
 constexpr int SCAN_NT = 1024;
 constexpr int SCAN_ITEMS = 8;
@@ -32,12 +32,32 @@ constexpr int SCAN_CHUNK = SCAN_NT * SCAN_ITEMS;
 
 enum : int { SRC_FIELD = 0, SRC_A = 1, SRC_B = 2, DST_A = 1, DST_B = 2, DST_ORDER = 3 };
 
+// passes 0-3: the four bytes of the key; passes 4-5: the two bytes of the
+// field index of a vertex when several fields are sorted at once (their
+// vertices are concatenated; each field gets its own order)
+constexpr int kPasses = 6;
+
 struct Plan {
-  int active[4];
-  int src[4];
-  int dst[4];
+  int active[kPasses];
+  int src[kPasses];
+  int dst[kPasses];
   int any;
 };
+
+struct Fields {
+  const int64_t* off;  // nfields + 1 vertex offsets (device), or null for one field
+  int n;
+};
+
+__device__ __forceinline__ uint32_t field_of(const Fields& fl, uint32_t v) {
+  int lo = 0, hi = fl.n;  // largest i with off[i] <= v
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(fl.off + mid) <= (int64_t)v) lo = mid;
+    else hi = mid;
+  }
+  return (uint32_t)lo;
+}
 
 __device__ __forceinline__ uint32_t canon_key(float v, bool* nan) {
   uint32_t b = __float_as_uint(v);
@@ -64,23 +84,26 @@ __global__ void __launch_bounds__(256) hist_all_kernel(const float* __restrict__
     if ((&h[0][0])[i]) atomicAdd(ghist + i, (&h[0][0])[i]);
 }
 
-__global__ void plan_kernel(const unsigned int* __restrict__ ghist, int64_t n, Plan* plan) {
+__global__ void plan_kernel(const unsigned int* __restrict__ ghist, int64_t n, int nfields,
+                            Plan* plan) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  int act[4];
+  int act[kPasses];
   for (int p = 0; p < 4; ++p) {
     unsigned int mx = 0;
     for (int d = 0; d < 256; ++d) mx = max(mx, ghist[p * 256 + d]);
     act[p] = (int64_t)mx != n;
   }
+  act[4] = nfields > 1;
+  act[5] = nfields > 256;
   int last = -1, first = -1, cnt = 0;
-  for (int p = 0; p < 4; ++p)
+  for (int p = 0; p < kPasses; ++p)
     if (act[p]) {
       if (first < 0) first = p;
       last = p;
       ++cnt;
     }
   int cur = SRC_FIELD, k = 0;
-  for (int p = 0; p < 4; ++p) {
+  for (int p = 0; p < kPasses; ++p) {
     plan->active[p] = act[p];
     plan->src[p] = plan->dst[p] = 0;
     if (!act[p]) continue;
@@ -100,12 +123,21 @@ __device__ __forceinline__ void load_key(int src, const float* f, const uint32_t
   else k = __ldg((src == SRC_A ? ka : kb) + i);
 }
 
+// digit of pass p: a key byte, or a byte of the vertex's field index
+__device__ __forceinline__ uint32_t digit_of(int pass, uint32_t key, uint32_t val, const Fields& fl) {
+  if (pass < 4) return (key >> (8 * pass)) & 255u;
+  return (field_of(fl, val) >> (8 * (pass - 4))) & 255u;
+}
+
 // per-tile digit counts, digit-major: th[d * ntiles + tile]
 __global__ void __launch_bounds__(SORT_NT) upsweep_kernel(int pass, const Plan* __restrict__ plan,
                                                           const float* __restrict__ f,
                                                           const uint32_t* __restrict__ ka,
                                                           const uint32_t* __restrict__ kb,
-                                                          int64_t n, int64_t ntiles,
+                                                          const uint32_t* __restrict__ va,
+                                                          const uint32_t* __restrict__ vb,
+                                                          const Fields fl, int64_t n,
+                                                          int64_t ntiles,
                                                           unsigned int* __restrict__ th) {
   if (!plan->active[pass]) return;
   const int src = plan->src[pass];
@@ -118,9 +150,10 @@ __global__ void __launch_bounds__(SORT_NT) upsweep_kernel(int pass, const Plan* 
     int64_t i = base + r * 32 + lane;
     uint32_t d = 256u + lane;  // unique dummy digit for the ragged tail
     if (i < n) {
-      uint32_t k;
-      load_key(src, f, ka, kb, i, k);
-      d = (k >> (8 * pass)) & 255u;
+      uint32_t k = 0, v = (uint32_t)i;
+      if (pass < 4) load_key(src, f, ka, kb, i, k);
+      else if (src != SRC_FIELD) v = __ldg((src == SRC_A ? va : vb) + i);
+      d = digit_of(pass, k, v, fl);
     }
     unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
     if (d < 256u && lane == __ffs(peers) - 1) h[warp][d] += __popc(peers);
@@ -229,10 +262,10 @@ struct DownSmem {
   uint32_t sv[SORT_TILE];
 };
 
-__global__ void __launch_bounds__(SORT_NT) downsweep_kernel(
+__global__ void __launch_bounds__(SORT_NT, 3) downsweep_kernel(
     int pass, const Plan* __restrict__ plan, const float* __restrict__ f, uint32_t* ka,
-    uint32_t* kb, uint32_t* va, uint32_t* vb, uint32_t* __restrict__ order, int64_t n,
-    int64_t ntiles, const unsigned int* __restrict__ th) {
+    uint32_t* kb, uint32_t* va, uint32_t* vb, uint32_t* __restrict__ order, const Fields fl,
+    int64_t n, int64_t ntiles, const unsigned int* __restrict__ th) {
   if (!plan->active[pass]) return;
   const int src = plan->src[pass], dst = plan->dst[pass];
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -255,7 +288,7 @@ __global__ void __launch_bounds__(SORT_NT) downsweep_kernel(
     if (i < n) {
       load_key(src, f, ka, kb, i, key[r]);
       val[r] = src == SRC_FIELD ? (uint32_t)i : __ldg(vsrc + i);
-      d = (key[r] >> (8 * pass)) & 255u;
+      d = digit_of(pass, key[r], val[r], fl);
     }
     unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
     unsigned int b = d < 256u ? sm.wh[warp][d] : 0u;
@@ -285,7 +318,7 @@ __global__ void __launch_bounds__(SORT_NT) downsweep_kernel(
   for (int r = 0; r < SORT_ITEMS; ++r) {
     int64_t i = base + r * 32 + lane;
     if (i < n) {
-      uint32_t d = (key[r] >> (8 * pass)) & 255u;
+      uint32_t d = digit_of(pass, key[r], val[r], fl);
       unsigned int p = sm.dstart[d] + sm.wh[warp][d] + pos[r];
       sm.sk[p] = key[r];
       sm.sv[p] = val[r];
@@ -297,10 +330,12 @@ __global__ void __launch_bounds__(SORT_NT) downsweep_kernel(
   uint32_t* vd = dst == DST_A ? va : vb;
   for (int p = threadIdx.x; p < cnt; p += SORT_NT) {
     uint32_t k = sm.sk[p];
-    uint32_t d = (k >> (8 * pass)) & 255u;
+    const uint32_t v = sm.sv[p];
+    uint32_t d = digit_of(pass, k, v, fl);
     uint32_t g = sm.goff[d] + (p - sm.dstart[d]);
     if (dst == DST_ORDER) {
-      order[sm.sv[p]] = g;
+      // position within the vertex's own field
+      order[v] = fl.n > 1 ? g - (uint32_t)__ldg(fl.off + field_of(fl, v)) : g;
     } else {
       kd[g] = k;
       vd[g] = sm.sv[p];
@@ -344,10 +379,19 @@ OrderWs carve_order(void* base, int64_t n) {
 }  // namespace
 
 size_t order_workspace_bytes(const Grid& g) { return carve_order(nullptr, g.n).bytes; }
+size_t order_workspace_bytes_n(int64_t n) { return carve_order(nullptr, n).bytes; }
+
+int launch_order_fields(const float* f, int64_t n, const int64_t* foff, int nfields,
+                        uint32_t* order, void* ws, int32_t* dstatus, cudaStream_t s);
 
 int launch_order(const float* f, const Grid& g, uint32_t* order, void* ws, int32_t* dstatus,
                  cudaStream_t s) {
-  const int64_t n = g.n;
+  return launch_order_fields(f, g.n, nullptr, 1, order, ws, dstatus, s);
+}
+
+int launch_order_fields(const float* f, int64_t n, const int64_t* foff, int nfields,
+                        uint32_t* order, void* ws, int32_t* dstatus, cudaStream_t s) {
+  const Fields fl{foff, nfields};
   OrderWs w = carve_order(ws, n);
   const int64_t ntiles = (n + SORT_TILE - 1) / SORT_TILE;
   const int64_t m = ntiles * 256;
@@ -365,14 +409,16 @@ int launch_order(const float* f, const Grid& g, uint32_t* order, void* ws, int32
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int64_t hb = std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
   hist_all_kernel<<<(unsigned)hb, 256, 0, s>>>(f, n, w.ghist, dstatus); count_launch();
-  plan_kernel<<<1, 32, 0, s>>>(w.ghist, n, w.plan); count_launch();
-  for (int p = 0; p < 4; ++p) {
-    upsweep_kernel<<<(unsigned)ntiles, SORT_NT, 0, s>>>(p, w.plan, f, w.ka, w.kb, n, ntiles, w.th); count_launch();
+  plan_kernel<<<1, 32, 0, s>>>(w.ghist, n, nfields, w.plan); count_launch();
+  const int passes = nfields > 256 ? 6 : (nfields > 1 ? 5 : 4);
+  for (int p = 0; p < passes; ++p) {
+    upsweep_kernel<<<(unsigned)ntiles, SORT_NT, 0, s>>>(p, w.plan, f, w.ka, w.kb, w.va, w.vb, fl, n,
+                                                        ntiles, w.th); count_launch();
     scan_reduce_kernel<<<(unsigned)nsums, SCAN_NT, 0, s>>>(p, w.plan, w.th, m, w.sums); count_launch();
     scan_sums_kernel<<<1, SCAN_NT, 0, s>>>(p, w.plan, w.sums, nsums); count_launch();
     scan_down_kernel<<<(unsigned)nsums, SCAN_NT, 0, s>>>(p, w.plan, w.th, m, w.sums); count_launch();
     downsweep_kernel<<<(unsigned)ntiles, SORT_NT, sizeof(DownSmem), s>>>(
-        p, w.plan, f, w.ka, w.kb, w.va, w.vb, order, n, ntiles, w.th); count_launch();
+        p, w.plan, f, w.ka, w.kb, w.va, w.vb, order, fl, n, ntiles, w.th); count_launch();
   }
   int64_t ib = std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
   identity_kernel<<<(unsigned)ib, 256, 0, s>>>(w.plan, order, n); count_launch();

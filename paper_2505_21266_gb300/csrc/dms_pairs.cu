@@ -746,3 +746,547 @@ int launch_diagram(const float* f, const uint32_t* order, const uint8_t* desc, c
 }
 
 }  // namespace dms
+
+// ===========================================================================
+// Batched form: many fields in one pass, nothing synchronising the host.
+// The critical lists hold GLOBAL ids (anchors in the concatenated arrays);
+// every field is traced with its own dims; the pairing runs a fixed number
+// of rounds on the device (sizes read from device memory) and finishes the
+// last few saddles in sorted order in one CTA.  D0 graphs of different
+// fields are disjoint; the D2 graphs share the OUTSIDE node, which is older
+// than every maximum, so each field's pairs are those it has alone.
+// ===========================================================================
+namespace dms {
+namespace {
+
+struct FieldTab {
+  const dms_field_desc* fd;
+  int n;
+};
+
+__device__ __forceinline__ int field_of_vertex(const FieldTab& ft, int64_t v) {
+  int lo = 0, hi = ft.n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (ft.fd[mid].offset <= v) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ Grid grid_of(const dms_field_desc& d) {
+  Grid g;
+  g.nx = d.nx;
+  g.ny = d.ny;
+  g.nz = d.nz;
+  g.sxy = (int64_t)d.nx * d.ny;
+  g.n = g.sxy * d.nz;
+  return g;
+}
+
+__device__ __forceinline__ int64_t slot_delta_of(const Grid& g, int s) {
+  const int k = s < 7 ? s : s - 7;
+  const int c = (0x7653421 >> (4 * k)) & 15;
+  const int64_t d = (c & 1) + ((c >> 1) & 1) * g.nx + ((c >> 2) & 1) * g.sxy;
+  return s < 7 ? d : -d;
+}
+
+// rank of u among the lower neighbours of t (global index, field offset off)
+__device__ __forceinline__ uint32_t local_rank_f(const Grid& g, int64_t off,
+                                                 const uint32_t* __restrict__ order, int64_t t,
+                                                 uint32_t ou) {
+  int64_t x, y, z;
+  xyz(g, t - off, x, y, z);
+  uint32_t r = 0;
+#pragma unroll
+  for (int s = 0; s < 14; ++s) {
+    const int c = (0x7653421 >> (4 * (s < 7 ? s : s - 7))) & 15;
+    const int sg = s < 7 ? 1 : -1;
+    const int64_t nx = x + sg * (c & 1), ny = y + sg * ((c >> 1) & 1), nz = z + sg * ((c >> 2) & 1);
+    if (nx < 0 || ny < 0 || nz < 0 || nx >= g.nx || ny >= g.ny || nz >= g.nz) continue;
+    r += __ldg(order + t + slot_delta_of(g, s)) < ou ? 1u : 0u;
+  }
+  return r;
+}
+
+__device__ __forceinline__ int64_t descend_f(const Grid& g, const uint8_t* __restrict__ desc,
+                                             int64_t v, int32_t* dstatus) {
+  for (int64_t it = 0; it < g.n; ++it) {
+    const uint8_t d = __ldg(desc + v);
+    if (d >= 14) return v;
+    v += slot_delta_of(g, d);
+  }
+  set_status(dstatus, DMS_ERR_TIMEOUT);
+  return v;
+}
+
+// global tet id t in field (g, off); -1 = OUTSIDE
+__device__ __forceinline__ int64_t ascend_f(const Grid& g, int64_t off,
+                                            const uint64_t* __restrict__ rec, int64_t t,
+                                            int32_t* dstatus) {
+  int64_t b = t / 6;
+  int k = (int)(t - b * 6);
+  int64_t bx, by, bz;
+  xyz(g, b - off, bx, by, bz);
+  for (int64_t it = 0; it < 6 * g.n; ++it) {
+    const uint32_t code = (uint32_t)(__ldg(rec + b) >> (33 + 3 * k)) & 7u;
+    if (code == 7u) return b * 6 + k;
+    if (code < 1u || code > 4u) {
+      set_status(dstatus, DMS_ERR_ARG);
+      return -1;
+    }
+    const int c1 = cTetC[k][0], c2 = cTetC[k][1];
+    int n1, n2, step = 0, sg = 0;
+    switch (code - 1) {
+      case 0: step = c1; sg = 1; n1 = c2 ^ c1; n2 = 7 ^ c1; break;
+      case 3: step = 7 ^ c2; sg = -1; n1 = step; n2 = step | c1; break;
+      case 1: n1 = c2 ^ c1; n2 = c2; break;
+      default: n1 = c1; n2 = c1 | (7 ^ c2); break;
+    }
+    if (sg) {
+      bx += sg * (step & 1);
+      by += sg * ((step >> 1) & 1);
+      bz += sg * ((step >> 2) & 1);
+      if (!fits(g, bx, by, bz, 7)) return -1;
+      b += sg * corner_delta(g, step);
+    }
+    k = tet_type(n1, n2);
+  }
+  set_status(dstatus, DMS_ERR_TIMEOUT);
+  return -1;
+}
+
+__global__ void b_build_dir(const int64_t* __restrict__ list, const int64_t* __restrict__ n_dev,
+                            int shift, uint32_t* start) {
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b > kDirBuckets) return;
+  const int64_t key = b << shift;
+  int64_t lo = 0, hi = *n_dev;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (list[mid] < key) lo = mid + 1;
+    else hi = mid;
+  }
+  start[b] = (uint32_t)lo;
+}
+
+__global__ void b_init_nodes_d0(const uint32_t* __restrict__ order, const int64_t* __restrict__ crit0,
+                                const int64_t* __restrict__ cnt, uint32_t* parent,
+                                unsigned long long* best, uint64_t* age) {
+  const int64_t n = cnt[0];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    parent[i] = (uint32_t)i;
+    best[i] = 0ull;
+    age[i] = __ldg(order + crit0[i]);
+  }
+}
+
+__global__ void b_essential(const FieldTab ft, const float* __restrict__ f,
+                            const uint32_t* __restrict__ order, const int64_t* __restrict__ crit0,
+                            const int64_t* __restrict__ cnt, dms_pair* ess) {
+  const int64_t n = cnt[0];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t m = crit0[i];
+    if (__ldg(order + m) != 0u) continue;  // each field's global minimum
+    const int fi = field_of_vertex(ft, m);
+    const int64_t lm = m - ft.fd[fi].offset;
+    dms_pair p;
+    p.birth_id = lm;
+    p.death_id = -1;
+    p.birth = __ldg(f + m);
+    p.death = __int_as_float(0x7F800000);
+    p.birth_vtx = (uint32_t)lm;
+    p.death_vtx = 0;
+    ess[fi] = p;
+  }
+}
+
+__global__ void b_d0_triplets(const FieldTab ft, const uint32_t* __restrict__ order,
+                              const uint8_t* __restrict__ desc, const Dir dir0,
+                              const int64_t* __restrict__ crit1, const int64_t* __restrict__ cnt,
+                              Tri T, uint32_t* live, unsigned int* live_n, int32_t* dstatus) {
+  const int64_t ne = cnt[1];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ne;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t id = crit1[i];
+    const int64_t a = id / 7;
+    const int k = (int)(id - a * 7);
+    const dms_field_desc fd = ft.fd[field_of_vertex(ft, a)];
+    const Grid g = grid_of(fd);
+    const int64_t b = a + corner_delta(g, cCornerOfEdge[k]);
+    const uint32_t oa = __ldg(order + a), ob = __ldg(order + b);
+    const int64_t top = oa > ob ? a : b;
+    const uint32_t r = local_rank_f(g, fd.offset, order, top, oa > ob ? ob : oa);
+    T.w[i] = ((uint64_t)(oa > ob ? oa : ob) << 4) | r;
+    T.res[i] = kNone;
+    const int64_t t0 = descend_f(g, desc, a, dstatus), t1 = descend_f(g, desc, b, dstatus);
+    if (t0 == t1) continue;
+    const int64_t n0 = dir_find(dir0, t0), n1 = dir_find(dir0, t1);
+    if (n0 < 0 || n1 < 0) {
+      set_status(dstatus, DMS_ERR_ARG);
+      continue;
+    }
+    T.na[i] = (uint32_t)n0;
+    T.nb[i] = (uint32_t)n1;
+    append(live, live_n, (uint32_t)i);
+  }
+}
+
+__global__ void b_init_nodes_d2(const FieldTab ft, const uint32_t* __restrict__ order,
+                                const int64_t* __restrict__ crit3, const int64_t* __restrict__ cnt,
+                                uint32_t* parent, unsigned long long* best, uint64_t* age) {
+  const int64_t nmax = cnt[3];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= nmax;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    parent[i] = (uint32_t)i;
+    best[i] = 0ull;
+    if (i == 0) {
+      age[0] = 0;  // OUTSIDE is older than every maximum of every field
+      continue;
+    }
+    const int64_t id = crit3[i - 1];
+    const int64_t a = id / 6;
+    const int k = (int)(id - a * 6);
+    const dms_field_desc fd = ft.fd[field_of_vertex(ft, a)];
+    const Grid g = grid_of(fd);
+    const int cs[4] = {0, cTetC[k][0], cTetC[k][1], 7};
+    int64_t v[4];
+    uint32_t o[4];
+    int it = 0;
+    for (int j = 0; j < 4; ++j) {
+      v[j] = a + corner_delta(g, cs[j]);
+      o[j] = __ldg(order + v[j]);
+      if (o[j] > o[it]) it = j;
+    }
+    uint32_t r[3];
+    int n = 0;
+    for (int j = 0; j < 4; ++j)
+      if (j != it) r[n++] = local_rank_f(g, fd.offset, order, v[it], o[j]);
+    const uint32_t h = max(r[0], max(r[1], r[2])), l = min(r[0], min(r[1], r[2]));
+    const uint32_t m = r[0] + r[1] + r[2] - h - l;
+    const uint64_t key = ((uint64_t)o[it] << 12) | (h << 8) | (m << 4) | l;
+    age[i] = (kMask44 - key) + 1;
+  }
+}
+
+__global__ void b_d2_triplets(const FieldTab ft, const uint32_t* __restrict__ order,
+                              const uint64_t* __restrict__ rec, const Dir dir3,
+                              const int64_t* __restrict__ crit2, const int64_t* __restrict__ cnt,
+                              Tri T, uint32_t* live, unsigned int* live_n, int32_t* dstatus) {
+  const int64_t nt = cnt[2];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nt;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t id = crit2[i];
+    const int64_t a = id / 12;
+    const int k = (int)(id - a * 12);
+    const dms_field_desc fd = ft.fd[field_of_vertex(ft, a)];
+    const Grid g = grid_of(fd);
+    const int p = cTriPQ[k][0], q = cTriPQ[k][1];
+    int64_t v[3] = {a, a + corner_delta(g, p), a + corner_delta(g, q)};
+    uint32_t o[3] = {__ldg(order + v[0]), __ldg(order + v[1]), __ldg(order + v[2])};
+    int it = 0;
+    if (o[1] > o[it]) it = 1;
+    if (o[2] > o[it]) it = 2;
+    uint32_t om = 0, ol = 0xFFFFFFFFu;
+    for (int j = 0; j < 3; ++j)
+      if (j != it) {
+        om = max(om, o[j]);
+        ol = min(ol, o[j]);
+      }
+    const uint32_t rm = local_rank_f(g, fd.offset, order, v[it], om);
+    const uint32_t rl = local_rank_f(g, fd.offset, order, v[it], ol);
+    const uint64_t key = ((uint64_t)o[it] << 8) | (rm << 4) | rl;
+    T.w[i] = kMask44 - key;
+    T.res[i] = kNone;
+    int64_t ax, ay, az;
+    xyz(g, a - fd.offset, ax, ay, az);
+    int64_t cof[2] = {-1, -1};
+    if (q == 7) {
+      const int e = (__popc(p) == 1) ? (7 ^ p) : p;
+      const int e1 = e & -e, e2 = e ^ e1;
+      if (fits(g, ax, ay, az, 7)) {
+        if (__popc(p) == 1) {
+          cof[0] = a * 6 + tet_type(p, p | e1);
+          cof[1] = a * 6 + tet_type(p, p | e2);
+        } else {
+          cof[0] = a * 6 + tet_type(e1, p);
+          cof[1] = a * 6 + tet_type(e2, p);
+        }
+      }
+    } else {
+      if (fits(g, ax, ay, az, 7)) cof[0] = a * 6 + tet_type(p, q);
+      const int e = 7 ^ q;
+      const int64_t bx = ax - (e & 1), by = ay - ((e >> 1) & 1), bz = az - ((e >> 2) & 1);
+      if (fits(g, bx, by, bz, 7)) cof[1] = (a - corner_delta(g, e)) * 6 + tet_type(e, e | p);
+    }
+    int64_t end[2];
+    for (int j = 0; j < 2; ++j) end[j] = cof[j] < 0 ? -1 : ascend_f(g, fd.offset, rec, cof[j], dstatus);
+    if (end[0] == end[1]) continue;
+    int64_t node[2];
+    bool ok = true;
+    for (int j = 0; j < 2; ++j) {
+      if (end[j] < 0) {
+        node[j] = 0;
+      } else {
+        const int64_t pos = dir_find(dir3, end[j]);
+        if (pos < 0) ok = false;
+        node[j] = pos + 1;
+      }
+    }
+    if (!ok) {
+      set_status(dstatus, DMS_ERR_ARG);
+      continue;
+    }
+    T.na[i] = (uint32_t)node[0];
+    T.nb[i] = (uint32_t)node[1];
+    append(live, live_n, (uint32_t)i);
+  }
+}
+
+// the saddles still live after the rounds, finished in increasing weight in
+// one CTA: bitonic sort in shared memory, then one thread runs Alg. 1
+constexpr int kFinishMax = 4096;
+__global__ void __launch_bounds__(1024) b_finish(const uint32_t* __restrict__ live,
+                                                 const unsigned int* __restrict__ live_n, Tri T,
+                                                 uint32_t* parent, const uint64_t* __restrict__ age,
+                                                 int32_t* dstatus) {
+  __shared__ unsigned long long key[kFinishMax];
+  __shared__ uint32_t idx[kFinishMax];
+  const unsigned int n = *live_n;
+  if (n == 0) return;
+  if (n > (unsigned)kFinishMax) {
+    if (threadIdx.x == 0) set_status(dstatus, DMS_ERR_TIMEOUT);
+    return;
+  }
+  for (int i = threadIdx.x; i < kFinishMax; i += blockDim.x) {
+    key[i] = i < (int)n ? T.w[live[i]] : ~0ull;
+    idx[i] = i < (int)n ? live[i] : kNone;
+  }
+  __syncthreads();
+  for (int size = 2; size <= kFinishMax; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < kFinishMax; i += blockDim.x) {
+        const int j = i ^ stride;
+        if (j > i) {
+          const bool up = (i & size) == 0;
+          if ((key[i] > key[j]) == up) {
+            const unsigned long long tk = key[i];
+            key[i] = key[j];
+            key[j] = tk;
+            const uint32_t ti = idx[i];
+            idx[i] = idx[j];
+            idx[j] = ti;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  if (threadIdx.x != 0) return;
+  for (unsigned int j = 0; j < n; ++j) {
+    const uint32_t i = idx[j];
+    uint32_t a = T.na[i], b = T.nb[i];
+    while (parent[a] != a) a = parent[a] = parent[parent[a]];
+    while (parent[b] != b) b = parent[b] = parent[parent[b]];
+    if (a == b) continue;
+    const uint32_t young = age[a] > age[b] ? a : b;
+    parent[young] = young == a ? b : a;
+    T.res[i] = young;
+  }
+}
+
+// per-field pair counts, then offsets (one CTA; fields are few)
+__global__ void b_count_fields(const FieldTab ft, const Tri T, const int64_t* __restrict__ crit,
+                               const int64_t* __restrict__ n_dev, int per_anchor,
+                               unsigned long long* fcount) {
+  const int64_t n = *n_dev;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (T.res[i] != kNone) atomicAdd(fcount + field_of_vertex(ft, crit[i] / per_anchor), 1ull);
+}
+
+__global__ void b_field_offsets(const unsigned long long* __restrict__ fcount, int nfields,
+                                int64_t* offsets, int64_t* total, int64_t cap, int32_t* dstatus) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int64_t acc = 0;
+  for (int f = 0; f < nfields; ++f) {
+    offsets[f] = acc;
+    acc += (int64_t)fcount[f];
+  }
+  offsets[nfields] = acc;
+  *total = acc;
+  if (acc > cap) set_status(dstatus, DMS_ERR_CAPACITY);
+}
+
+// pairs in saddle order (= field order), ids made local to the field
+__global__ void __launch_bounds__(PNT) b_count_pairs(const Tri T, const int64_t* __restrict__ n_dev,
+                                                     long long* tc) {
+  __shared__ long long tmp[32];
+  const int64_t nsad = *n_dev;
+  const int64_t base = (int64_t)blockIdx.x * PTILE + (int64_t)threadIdx.x * PITEMS;
+  int c = 0;
+  for (int k = 0; k < PITEMS; ++k) {
+    const int64_t i = base + k;
+    if (i < nsad && T.res[i] != kNone) ++c;
+  }
+  long long t;
+  scan64::block_excl(c, tmp, &t);
+  if (threadIdx.x == 0) tc[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(PNT) b_write_pairs(int dim, const FieldTab ft,
+                                                     const float* __restrict__ f,
+                                                     const uint32_t* __restrict__ order,
+                                                     const int64_t* __restrict__ critA,
+                                                     const int64_t* __restrict__ critB, const Tri T,
+                                                     const int64_t* __restrict__ n_dev,
+                                                     const long long* __restrict__ toff,
+                                                     dms_pair* out, int64_t cap) {
+  __shared__ long long tmp[32];
+  const int64_t nsad = *n_dev;
+  const int64_t base = (int64_t)blockIdx.x * PTILE + (int64_t)threadIdx.x * PITEMS;
+  int c = 0;
+  for (int k = 0; k < PITEMS; ++k) {
+    const int64_t i = base + k;
+    if (i < nsad && T.res[i] != kNone) ++c;
+  }
+  long long pos = scan64::block_excl(c, tmp, nullptr) + toff[blockIdx.x];
+  for (int k = 0; k < PITEMS; ++k) {
+    const int64_t i = base + k;
+    if (i >= nsad || T.res[i] == kNone) continue;
+    if (pos < cap) {
+      dms_pair p;
+      if (dim == 0) {
+        const int64_t m = critA[T.res[i]];
+        const int64_t id = critB[i];
+        const int64_t a = id / 7;
+        const int kk = (int)(id - a * 7);
+        const dms_field_desc fd = ft.fd[field_of_vertex(ft, a)];
+        const Grid g = grid_of(fd);
+        int64_t v[2] = {a, a + corner_delta(g, cCornerOfEdge[kk])};
+        const int64_t top = top_of(Dev{}, order, v, 2);
+        p.birth_id = m - fd.offset;
+        p.death_id = id - 7 * fd.offset;
+        p.birth = __ldg(f + m);
+        p.death = __ldg(f + top);
+        p.birth_vtx = (uint32_t)(m - fd.offset);
+        p.death_vtx = (uint32_t)(top - fd.offset);
+      } else {
+        const int64_t tet = critB[T.res[i] - 1];
+        const int64_t tri = critA[i];
+        const int64_t a = tri / 12;
+        const int kk = (int)(tri - a * 12);
+        const dms_field_desc fd = ft.fd[field_of_vertex(ft, a)];
+        const Grid g = grid_of(fd);
+        int64_t tv[3] = {a, a + corner_delta(g, cTriPQ[kk][0]), a + corner_delta(g, cTriPQ[kk][1])};
+        const int64_t b = tet / 6;
+        const int kq = (int)(tet - b * 6);
+        int64_t qv[4] = {b, b + corner_delta(g, cTetC[kq][0]), b + corner_delta(g, cTetC[kq][1]),
+                         b + corner_delta(g, 7)};
+        const int64_t st = top_of(Dev{}, order, tv, 3), qt = top_of(Dev{}, order, qv, 4);
+        p.birth_id = tri - 12 * fd.offset;
+        p.death_id = tet - 6 * fd.offset;
+        p.birth = __ldg(f + st);
+        p.death = __ldg(f + qt);
+        p.birth_vtx = (uint32_t)(st - fd.offset);
+        p.death_vtx = (uint32_t)(qt - fd.offset);
+      }
+      out[pos] = p;
+    }
+    ++pos;
+  }
+}
+
+}  // namespace
+
+constexpr int kBatchRounds = 96;
+int diagram_batch_rounds() { return kBatchRounds; }
+
+// Workspace of the batched pairing: the DiagWs of the capacities plus the
+// per-field counters and pair-tile sums.
+size_t diagram_batch_workspace_bytes(int64_t nfields, const int64_t* caps) {
+  WsCarver c(nullptr);
+  c.take<unsigned char>(carve_diag(nullptr, caps).bytes);
+  const int64_t nsad = std::max<int64_t>(std::max<int64_t>(caps[1], caps[2]), 1);
+  const int64_t ntiles = (nsad + PTILE - 1) / PTILE;
+  c.take<unsigned long long>(2 * (nfields + 1));
+  c.take<long long>(ntiles + 1);
+  c.take<long long>(scan64::num_sums(ntiles) + 1);
+  return c.used;
+}
+
+int launch_diagram_batch(const float* f, const uint32_t* order, const uint8_t* desc,
+                         const uint64_t* rec, const dms_field_desc* fields_dev, int nfields,
+                         int64_t total_vertices, int64_t* const crit[4], const int64_t* cnt_dev,
+                         const int64_t* caps, dms_pair* d0, dms_pair* d2, int64_t cap_pairs,
+                         int64_t* pair_offsets, dms_pair* ess, int64_t* pair_totals, void* ws,
+                         int32_t* dstatus, cudaStream_t s) {
+  WsCarver c(ws);
+  unsigned char* dbase = c.take<unsigned char>(carve_diag(nullptr, caps).bytes);
+  DiagWs w = carve_diag(dbase, caps);
+  const int64_t nsad = std::max<int64_t>(std::max<int64_t>(caps[1], caps[2]), 1);
+  const int64_t ntiles = (nsad + PTILE - 1) / PTILE;
+  unsigned long long* fcount = c.take<unsigned long long>(2 * (nfields + 1));
+  long long* tc = c.take<long long>(ntiles + 1);
+  long long* sums = c.take<long long>(scan64::num_sums(ntiles) + 1);
+  const FieldTab ft{fields_dev, nfields};
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const unsigned G = (unsigned)sms * 8, TB = 256;  // grid-stride launches
+  const unsigned dir_blocks = (unsigned)((kDirBuckets + TB) / TB);
+  const int shift0 = dir_shift(total_vertices), shift3 = dir_shift(6 * total_vertices);
+  DMS_CUDA_OK(cudaMemsetAsync(fcount, 0, 2 * (nfields + 1) * sizeof(unsigned long long), s));
+
+  bool mem_ok = true;
+  auto rounds = [&](Tri T) {
+    uint32_t* cur = w.live0;
+    uint32_t* nxt = w.live1;
+    unsigned int* cur_n = w.ctr + 0;
+    unsigned int* nxt_n = w.ctr + 1;
+    for (int r = 1; r <= kBatchRounds; ++r) {
+      mem_ok = mem_ok && cudaMemsetAsync(nxt_n, 0, sizeof(unsigned int), s) == cudaSuccess;
+      round_find<<<G, TB, 0, s>>>(cur, cur_n, T, w.parent, w.best, (uint64_t)r); count_launch();
+      round_merge<<<G, TB, 0, s>>>(cur, cur_n, T, w.parent, w.best, w.age, (uint64_t)r, nxt, nxt_n); count_launch();
+      std::swap(cur, nxt);
+      std::swap(cur_n, nxt_n);
+    }
+    b_finish<<<1, 1024, 0, s>>>(cur, cur_n, T, w.parent, w.age, dstatus); count_launch();
+  };
+  auto write = [&](int dim, Tri T, const int64_t* critA, const int64_t* critB, const int64_t* n_dev,
+                   dms_pair* out, int64_t* offs, int64_t* total, unsigned long long* fc) {
+    b_count_pairs<<<(unsigned)ntiles, PNT, 0, s>>>(T, n_dev, tc); count_launch();
+    scan64::run(tc, ntiles, sums, s);
+    b_write_pairs<<<(unsigned)ntiles, PNT, 0, s>>>(dim, ft, f, order, critA, critB, T, n_dev, tc,
+                                                   out, cap_pairs); count_launch();
+    b_count_fields<<<G, TB, 0, s>>>(ft, T, dim == 0 ? critB : critA, n_dev, dim == 0 ? 7 : 12, fc); count_launch();
+    b_field_offsets<<<1, 32, 0, s>>>(fc, nfields, offs, total, cap_pairs, dstatus); count_launch();
+  };
+
+  // ---- D0
+  DMS_CUDA_OK(cudaMemsetAsync(w.ctr, 0, 8 * sizeof(unsigned int), s));
+  b_init_nodes_d0<<<G, TB, 0, s>>>(order, crit[0], cnt_dev, w.parent, w.best, w.age); count_launch();
+  b_essential<<<G, TB, 0, s>>>(ft, f, order, crit[0], cnt_dev, ess); count_launch();
+  b_build_dir<<<dir_blocks, TB, 0, s>>>(crit[0], cnt_dev + 0, shift0, w.dir); count_launch();
+  const Dir dir0{crit[0], caps[0], w.dir, shift0};
+  b_d0_triplets<<<G, TB, 0, s>>>(ft, order, desc, dir0, crit[1], cnt_dev, w.T0, w.live0, w.ctr + 0,
+                                 dstatus); count_launch();
+  rounds(w.T0);
+  write(0, w.T0, crit[0], crit[1], cnt_dev + 1, d0, pair_offsets, pair_totals + 0, fcount);
+
+  // ---- D2
+  DMS_CUDA_OK(cudaMemsetAsync(w.ctr, 0, 8 * sizeof(unsigned int), s));
+  b_init_nodes_d2<<<G, TB, 0, s>>>(ft, order, crit[3], cnt_dev, w.parent, w.best, w.age); count_launch();
+  b_build_dir<<<dir_blocks, TB, 0, s>>>(crit[3], cnt_dev + 3, shift3, w.dir); count_launch();
+  const Dir dir3{crit[3], caps[3], w.dir, shift3};
+  b_d2_triplets<<<G, TB, 0, s>>>(ft, order, rec, dir3, crit[2], cnt_dev, w.T2, w.live0, w.ctr + 0,
+                                 dstatus); count_launch();
+  rounds(w.T2);
+  write(2, w.T2, crit[2], crit[3], cnt_dev + 2, d2, pair_offsets + (nfields + 1), pair_totals + 1,
+        fcount + (nfields + 1));
+  if (!mem_ok) return DMS_ERR_CUDA;
+  return launch_status();
+}
+
+}  // namespace dms

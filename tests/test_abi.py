@@ -15,7 +15,7 @@ HEADER = os.path.join(ROOT, "include", "dms.h")
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"\b(?:int|int64_t|size_t|const char\s*\*)\s+(dms_\w+)\s*\(", text)
+    names = re.findall(r"\b(?:int|int32_t|int64_t|size_t|const char\s*\*)\s+(dms_\w+)\s*\(", text)
     return sorted(set(names))
 
 
@@ -58,3 +58,28 @@ def test_host_side_validation(lib):
     for code in range(10):
         assert lib.dms_status_string(code)
     assert lib.dms_order_workspace_size(good) > 0
+
+
+def test_batch_host_validation(lib):
+    from paper_2505_21266_gb300 import _lib
+    assert lib.dms_batch_tile_variants() == 3
+    assert lib.dms_batch_max_rounds() > 0
+    T = _lib.dms_field_desc * 2
+    good = T(_lib.dms_field_desc(0, 4, 5, 6, 0), _lib.dms_field_desc(120, 3, 3, 3, 0))
+    gap = T(_lib.dms_field_desc(0, 4, 5, 6, 0), _lib.dms_field_desc(121, 3, 3, 3, 0))
+    thin = T(_lib.dms_field_desc(0, 4, 5, 6, 0), _lib.dms_field_desc(120, 1, 3, 3, 0))
+    caps = (ctypes.c_int64 * 4)(10, 10, 10, 10)
+    assert lib.dms_batch_workspace_size(ctypes.byref(good), 2, caps, 10) > 0
+    assert lib.dms_batch_workspace_size(ctypes.byref(gap), 2, caps, 10) == 0
+    assert lib.dms_batch_workspace_size(ctypes.byref(thin), 2, caps, 10) == 0
+    assert lib.dms_batch_workspace_size(ctypes.byref(good), 0, caps, 10) == 0
+    neg = (ctypes.c_int64 * 4)(10, -1, 10, 10)
+    assert lib.dms_batch_workspace_size(ctypes.byref(good), 2, neg, 10) == 0
+    fake = ctypes.c_void_p(0x1000)
+    args = lambda table, variant, wsb: lib.dms_batch_diagrams(
+        fake, ctypes.byref(table), fake, 2, variant, fake, fake, fake, caps, 10, fake, fake, fake,
+        fake, fake, fake, wsb, fake, None)
+    assert args(gap, 0, 1 << 40) == 8     # DMS_ERR_ARG: offsets not contiguous
+    assert args(thin, 0, 1 << 40) == 2    # DMS_ERR_DIMS
+    assert args(good, 3, 1 << 40) == 8    # no such tile variant
+    assert args(good, 0, 16) == 5         # DMS_ERR_WORKSPACE

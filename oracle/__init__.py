@@ -72,6 +72,10 @@ def _load():
         lib.orc_pair_extrema_saddles.argtypes = [i64, vp, vp, i64, vp, vp]
         lib.orc_lower_star_vertex.restype = ctypes.c_int
         lib.orc_lower_star_vertex.argtypes = [vp, i64, i64, i64, i64, vp, i64, vp, vp, i64, vp]
+        for name in ("orc_d0_edge_local", "orc_d2_triangle_local"):
+            fn = getattr(lib, name)
+            fn.restype = ctypes.c_int
+            fn.argtypes = [vp, i64, i64, i64, i64, i64, vp]
         _lib = lib
     return _lib
 
@@ -164,3 +168,26 @@ def lower_star_vertex(field: np.ndarray, v: int):
     if rc:
         raise OracleError("lower star capacity")
     return pairs[: n_p.value].copy(), crit[: n_c.value].copy()
+
+
+def _local(name, field, sid, limit):
+    f = np.ascontiguousarray(field, dtype=np.float32)
+    nz, ny, nx = f.shape
+    out = ctypes.c_int64(-3)
+    rc = getattr(_load(), name)(f.ctypes.data, nx, ny, nz, int(sid), int(limit), ctypes.byref(out))
+    if rc == -2:
+        raise OracleError("no such simplex")
+    return rc, int(out.value)
+
+
+def d0_edge_local(field: np.ndarray, edge: int, limit: int = 1 << 62):
+    """Elder rule at one edge, by growing the two sublevel components at its
+    ends (Sec. 2.4): (1, dying minimum) if the edge kills a component, (0, -3)
+    if its ends are already connected, (-1, -3) past `limit` vertices."""
+    return _local("orc_d0_edge_local", field, edge, limit)
+
+
+def d2_triangle_local(field: np.ndarray, tri: int, limit: int = 1 << 62):
+    """Dual elder rule at one triangle on tetrahedra + the outside:
+    (1, dying tetrahedron), (0, -3) or (-1, -3) as in d0_edge_local."""
+    return _local("orc_d2_triangle_local", field, tri, limit)

@@ -32,8 +32,10 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <deque>
 #include <limits>
 #include <queue>
+#include <unordered_map>
 #include <utility>
 #include <vector>
 
@@ -707,6 +709,63 @@ void compute_reduction(Context& c) {
 // ---------------------------------------------------------------------------
 // C interface (loaded with ctypes by the tests)
 // ---------------------------------------------------------------------------
+
+// ---------------------------------------------------------------------------
+// Local elder-rule checks, straight from the field (for sampled outputs of
+// grids too large for the full oracle).
+//
+// D0 is the 0-dimensional persistence of the lexicographic lower-star
+// filtration (Sec. 2.1, Sec. 2.4): an edge e = {l < t} enters after every
+// vertex up to t and every edge with a smaller key.  If its two ends lie in
+// different components of what came before, e kills the younger component,
+// the one whose lowest vertex is higher (the elder rule); otherwise e closes
+// a loop and is no D0 death.  D2 is the same statement on the dual graph in
+// the reversed filtration: tetrahedra are the nodes, a triangle joins its two
+// cofacets (or its one cofacet and the outside), the triangles enter by
+// decreasing key, and the component whose highest tetrahedron is lower dies;
+// the outside is higher than every tetrahedron.
+//
+// Both checks grow the two components from the two ends of the simplex in
+// lockstep by breadth-first search, so that they stop as soon as one of them
+// is exhausted.  They share nothing with the v-path tracing or with Alg. 1.
+// ---------------------------------------------------------------------------
+namespace elder {
+
+// vertex u below vertex w in the filtration: (f with -0 == +0, offset)
+bool vless(const float* f, int64_t u, int64_t w) {
+  double a = canon(f[u]), b = canon(f[w]);
+  return a < b || (a == b && u < w);
+}
+
+// vertices of a simplex listed from the highest down
+void sort_down(const float* f, int m, int64_t* v) {
+  std::sort(v, v + m, [f](int64_t a, int64_t b) { return vless(f, b, a); });
+}
+
+// -1, 0, 1: simplex a below, equal to, above simplex b (same dimension;
+// each list sorted from the highest vertex down)
+int cmp_down(const float* f, int m, const int64_t* a, const int64_t* b) {
+  for (int i = 0; i < m; ++i) {
+    if (a[i] == b[i]) continue;
+    return vless(f, a[i], b[i]) ? -1 : 1;
+  }
+  return 0;
+}
+
+// the 14 neighbours of a vertex (the other ends of its edges), -1 if outside
+void neighbours(const Grid& g, int64_t u, int64_t out[14]) {
+  int64_t x, y, z;
+  g.xyz(u, x, y, z);
+  for (int k = 0; k < 7; ++k) {
+    const int c = kEdgeCorner[k];
+    const int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
+    out[k] = g.inside(x + dx, y + dy, z + dz) ? g.at(x + dx, y + dy, z + dz) : -1;
+    out[7 + k] = g.inside(x - dx, y - dy, z - dz) ? g.at(x - dx, y - dy, z - dz) : -1;
+  }
+}
+
+}  // namespace elder
+
 extern "C" {
 
 enum {
@@ -836,6 +895,177 @@ int orc_lower_star_vertex(const float* f, int64_t nx, int64_t ny, int64_t nz, in
   std::copy(run.pairs.begin(), run.pairs.end(), pairs);
   std::copy(run.crits.begin(), run.crits.end(), crit);
   return 0;
+}
+
+// D0 at one edge (see the elder-rule notes above).  Returns 1 when the edge
+// joins two different components and writes the lowest vertex of the younger
+// one (the minimum the edge kills) to *dying; 0 when both ends are already
+// connected (no D0 pair); -1 when `limit` vertices were visited first.
+int orc_d0_edge_local(const float* f, int64_t nx, int64_t ny, int64_t nz, int64_t edge,
+                      int64_t limit, int64_t* dying) {
+  Grid g{nx, ny, nz, nx * ny * nz};
+  int64_t ev[4];
+  if (simplex_vertices(g, 1, edge, ev) != 2) return -2;
+  elder::sort_down(f, 2, ev);  // ev[0] = t (top), ev[1] = l
+  // edge {u, w} entered before e
+  auto before = [&](int64_t u, int64_t w) {
+    int64_t k[2] = {u, w};
+    elder::sort_down(f, 2, k);
+    return elder::cmp_down(f, 2, k, ev) < 0;
+  };
+  std::unordered_map<int64_t, int> side;
+  std::deque<int64_t> q[2];
+  int64_t low[2];
+  for (int s = 0; s < 2; ++s) {
+    side[ev[s]] = s;
+    q[s].push_back(ev[s]);
+    low[s] = ev[s];
+  }
+  int64_t visited = 2;
+  int done = -1;  // the side found exhausted first
+  // lockstep growth until one side is exhausted or the two meet
+  while (done < 0) {
+    for (int s = 0; s < 2 && done < 0; ++s) {
+      if (q[s].empty()) { done = s; break; }
+      int64_t u = q[s].front();
+      q[s].pop_front();
+      int64_t nb[14];
+      elder::neighbours(g, u, nb);
+      for (int j = 0; j < 14; ++j) {
+        int64_t w = nb[j];
+        if (w < 0 || !before(u, w)) continue;
+        auto it = side.find(w);
+        if (it != side.end()) {
+          if (it->second != s) return 0;  // the two ends are connected
+          continue;
+        }
+        side[w] = s;
+        q[s].push_back(w);
+        if (elder::vless(f, w, low[s])) low[s] = w;
+        if (++visited > limit) return -1;
+      }
+    }
+  }
+  // side `done` is a whole component; grow the other one until it shows a
+  // vertex below low[done] (then done's minimum dies) or is exhausted too
+  const int o = 1 - done;
+  if (elder::vless(f, low[o], low[done])) { *dying = low[done]; return 1; }
+  while (!q[o].empty()) {
+    int64_t u = q[o].front();
+    q[o].pop_front();
+    int64_t nb[14];
+    elder::neighbours(g, u, nb);
+    for (int j = 0; j < 14; ++j) {
+      int64_t w = nb[j];
+      if (w < 0 || !before(u, w) || side.count(w)) continue;
+      side[w] = o;
+      q[o].push_back(w);
+      if (elder::vless(f, w, low[done])) { *dying = low[done]; return 1; }
+      if (elder::vless(f, w, low[o])) low[o] = w;
+      if (++visited > limit) return -1;
+    }
+  }
+  *dying = low[o];
+  return 1;
+}
+
+// D2 at one triangle (dual statement).  Returns 1 when the triangle joins two
+// different components of the dual graph and writes the highest tetrahedron
+// of the younger one (the maximum it kills) to *dying; 0 when its cofacets
+// are already connected (no D2 pair); -1 past `limit` visited tetrahedra.
+int orc_d2_triangle_local(const float* f, int64_t nx, int64_t ny, int64_t nz, int64_t tri,
+                          int64_t limit, int64_t* dying) {
+  Grid g{nx, ny, nz, nx * ny * nz};
+  int64_t sv[4];
+  if (simplex_vertices(g, 2, tri, sv) != 3) return -2;
+  elder::sort_down(f, 3, sv);
+  const int64_t kOut = -1;  // the outside
+  auto tri_after = [&](int64_t t) {  // triangle t entered before tri (reversed)
+    int64_t v[4];
+    simplex_vertices(g, 2, t, v);
+    elder::sort_down(f, 3, v);
+    return elder::cmp_down(f, 3, v, sv) > 0;
+  };
+  auto tet_above = [&](int64_t a, int64_t b) {  // tet a above tet b
+    if (a == kOut) return b != kOut;
+    if (b == kOut) return false;
+    int64_t va[4], vb[4];
+    simplex_vertices(g, 3, a, va);
+    simplex_vertices(g, 3, b, vb);
+    elder::sort_down(f, 4, va);
+    elder::sort_down(f, 4, vb);
+    return elder::cmp_down(f, 4, va, vb) > 0;
+  };
+  // the nodes across the facets of tet q that entered before tri
+  auto across = [&](int64_t q, std::vector<int64_t>& out) {
+    out.clear();
+    int64_t v[4];
+    simplex_vertices(g, 3, q, v);
+    for (int drop = 0; drop < 4; ++drop) {
+      int64_t fv[3];
+      int m = 0;
+      for (int i = 0; i < 4; ++i)
+        if (i != drop) fv[m++] = v[i];
+      int64_t t = simplex_id(g, 3, fv);
+      if (t < 0 || !tri_after(t)) continue;
+      std::vector<int64_t> cof = triangle_cofacets(g, t);
+      if (cof.size() == 1) out.push_back(kOut);
+      for (int64_t c : cof)
+        if (c != q) out.push_back(c);
+    }
+  };
+  std::vector<int64_t> cof = triangle_cofacets(g, tri);
+  if (cof.empty()) return -2;
+  int64_t start[2] = {cof[0], cof.size() > 1 ? cof[1] : kOut};
+  std::unordered_map<int64_t, int> side;
+  std::deque<int64_t> q[2];
+  int64_t high[2];
+  for (int s = 0; s < 2; ++s) {
+    side[start[s]] = s;
+    if (start[s] != kOut) q[s].push_back(start[s]);  // the outside is not grown
+    high[s] = start[s];
+  }
+  int64_t visited = 2;
+  std::vector<int64_t> nb;
+  int done = -1;
+  while (done < 0) {
+    for (int s = 0; s < 2 && done < 0; ++s) {
+      if (high[s] == kOut) continue;  // holds the outside: the older side
+      if (q[s].empty()) { done = s; break; }
+      int64_t u = q[s].front();
+      q[s].pop_front();
+      across(u, nb);
+      for (int64_t w : nb) {
+        auto it = side.find(w);
+        if (it != side.end()) {
+          if (it->second != s) return 0;
+          continue;
+        }
+        side[w] = s;
+        if (w != kOut) q[s].push_back(w);
+        if (tet_above(w, high[s])) high[s] = w;
+        if (++visited > limit) return -1;
+      }
+    }
+    if (done < 0 && high[0] == kOut && high[1] == kOut) return 0;
+  }
+  const int o = 1 - done;
+  if (tet_above(high[o], high[done])) { *dying = high[done]; return 1; }
+  while (!q[o].empty()) {
+    int64_t u = q[o].front();
+    q[o].pop_front();
+    across(u, nb);
+    for (int64_t w : nb) {
+      if (side.count(w)) continue;
+      side[w] = o;
+      if (w != kOut) q[o].push_back(w);
+      if (tet_above(w, high[done])) { *dying = high[done]; return 1; }
+      if (tet_above(w, high[o])) high[o] = w;
+      if (++visited > limit) return -1;
+    }
+  }
+  *dying = high[o];
+  return 1;
 }
 
 }  // extern "C"

@@ -352,3 +352,38 @@ def test_lower_star_vertex_from_field_matches_full_gradient(rng):
         exp_p = {p for p in gp if cx.max_vertex(cx.verts(p[0], p[1]), order) == v}
         exp_c = {c for c in crit if cx.max_vertex(cx.verts(*c), order) == v}
         assert mine_p == exp_p and mine_c == exp_c
+
+
+@pytest.mark.parametrize("shape", [(5, 6, 7), (4, 4, 9), (2, 3, 11)])
+def test_local_elder_rule_matches_full_diagrams(rng, shape):
+    """The local checks (components grown from the two ends of one simplex)
+    agree with the full D0 / D2 on every critical edge and triangle: they
+    report a death exactly for the pairs the diagrams hold, with the same
+    dying extremum; and every gradient vertex-edge pair is a zero-persistence
+    death of its top vertex."""
+    for f in fields(rng, shape):
+        r = oracle.run(f)
+        d0 = {int(p["death_id"]): int(p["birth_id"]) for p in r.get(oracle.D0)}
+        for e in r.crit(1):
+            st, dying = oracle.d0_edge_local(f, int(e))
+            if int(e) in d0:
+                assert st == 1 and dying == d0[int(e)]
+            else:
+                assert st == 0
+        d2 = {int(p["birth_id"]): int(p["death_id"]) for p in r.get(oracle.D2)}
+        for t in r.crit(2):
+            st, dying = oracle.d2_triangle_local(f, int(t))
+            if int(t) in d2:
+                assert st == 1 and dying == d2[int(t)]
+            else:
+                assert st == 0
+        gp = r.get(oracle.GRAD_PAIRS).reshape(-1, 3)
+        for dim, v, e in gp[gp[:, 0] == 0][:40]:
+            assert oracle.d0_edge_local(f, int(e)) == (1, int(v))
+
+
+def test_local_elder_rule_limit(rng):
+    f = rng.random((12, 12, 12)).astype(np.float32)
+    r = oracle.run(f, gradient=True, diagrams=False)
+    outcomes = {oracle.d0_edge_local(f, int(e), limit=3)[0] for e in r.crit(1)}
+    assert -1 in outcomes

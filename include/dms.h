@@ -194,14 +194,17 @@ int dms_critical_noalloc(const uint8_t* desc, const uint64_t* rec, dms_dims d, i
  * exact: a round merges every saddle that is the lightest live saddle of both
  * of its components, or the lightest of a component whose other side is
  * older; both choices are the ones Alg. 1 makes at that saddle's turn.
+ * Paths that meet share their tail: a walk that reaches a vertex (D0) or a
+ * tetrahedron (D2) another walk has passed stops and takes that walk's end.
  *   f, order, desc, rec   as above;  crit0..3 and n_crit (HOST array of 4)
- *                         from dms_critical.
+ *                         from dms_critical; n_crit[1], n_crit[2] < 2^30.
  *   d0   [cap0] out: D0 pairs in increasing edge-id order (n_crit[0]-1 of
  *        them for a grid, plus the essential class written to *d0_essential).
  *   d2   [cap2] out: D2 pairs in increasing triangle-id order (n_crit[3]).
  *   n_out [2] int64 out: numbers of D0 and D2 pairs (capacity errors as in
  *        dms_critical).
- *   ws   at least dms_diagram_workspace_size(d, n_crit) bytes.
+ *   ws   at least dms_diagram_workspace_size(d, n_crit) bytes (it includes
+ *        one 32-bit word per tetrahedron id, 24 bytes per vertex).
  * This call synchronises `stream` between pairing rounds (it reads the
  * number of live saddles on the host).
  */

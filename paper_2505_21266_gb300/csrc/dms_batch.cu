@@ -28,7 +28,7 @@ size_t critical_workspace_bytes(const Grid& g);
 int launch_critical(const uint8_t* desc, const uint64_t* rec, const Grid& g, int64_t* c0,
                     int64_t* c1, int64_t* c2, int64_t* c3, const int64_t cap[4], int64_t* counts,
                     void* ws, int32_t* dstatus, cudaStream_t s);
-size_t diagram_batch_workspace_bytes(int64_t nfields, const int64_t* caps);
+size_t diagram_batch_workspace_bytes(int64_t nfields, const int64_t* caps, int64_t total);
 int diagram_batch_rounds();
 int launch_diagram_batch(const float* f, const uint32_t* order, const uint8_t* desc,
                          const uint64_t* rec, const dms_field_desc* fields_dev, int nfields,
@@ -91,7 +91,7 @@ BatchWs carve_batch(void* base, int nfields, int64_t total, const int64_t* caps)
   Grid g{};
   g.n = total;
   w.crit_ws = c.take<unsigned char>(critical_workspace_bytes(g));
-  w.diag_ws = c.take<unsigned char>(diagram_batch_workspace_bytes(nfields, caps));
+  w.diag_ws = c.take<unsigned char>(diagram_batch_workspace_bytes(nfields, caps, total));
   w.bytes = c.used;
   return w;
 }
@@ -115,6 +115,8 @@ int check_fields(const dms_field_desc* fh, int nfields, int64_t* total) {
 bool check_caps(const int64_t* caps, int64_t cap_pairs) {
   for (int k = 0; k < 4; ++k)
     if (caps[k] < 0 || caps[k] >= 4294967295ll) return false;
+  // two walks per saddle, 31-bit walk ids
+  if (caps[1] >= (1ll << 30) || caps[2] >= (1ll << 30)) return false;
   return cap_pairs >= 0;
 }
 

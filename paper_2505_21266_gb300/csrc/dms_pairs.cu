@@ -106,17 +106,6 @@ __device__ __forceinline__ void local_rank2(const Dev& D, const uint32_t* __rest
   }
 }
 
-__device__ __forceinline__ int64_t descend(const Dev& D, const uint8_t* __restrict__ desc,
-                                           int64_t v, int32_t* dstatus) {
-  for (int64_t it = 0; it < D.g.n; ++it) {
-    uint8_t d = __ldg(desc + v);
-    if (d >= 14) return v;
-    v += D.slot_delta[d];
-  }
-  set_status(dstatus, DMS_ERR_TIMEOUT);
-  return v;
-}
-
 // tet type of the chain 0 < c1 < c2 < 7 (index [c1][c2]), -1 if none
 __constant__ signed char cTetTypeOf[8][8] = {
     {-1, -1, -1, -1, -1, -1, -1, -1}, {-1, -1, -1, 0, -1, 1, -1, -1},
@@ -126,56 +115,29 @@ __constant__ signed char cTetTypeOf[8][8] = {
 
 __device__ __forceinline__ int tet_type(int c1, int c2) { return cTetTypeOf[c1][c2]; }
 
-// ascending dual v-path from tet t; -1 = OUTSIDE.  The walk keeps the
-// anchor's coordinates and linear offset and only adds corner deltas.
-__device__ __forceinline__ int64_t ascend(const Dev& D, const uint64_t* __restrict__ rec, int64_t t,
-                                          int32_t* dstatus) {
-  int64_t b = t / 6;
-  int k = (int)(t - b * 6);
-  int64_t bx, by, bz;
-  xyz(D.g, b, bx, by, bz);
-  for (int64_t it = 0; it < 6 * D.g.n; ++it) {
-    uint32_t code = (uint32_t)(__ldg(rec + b) >> (33 + 3 * k)) & 7u;
-    if (code == 7u) return b * 6 + k;
-    if (code < 1u || code > 4u) {
-      set_status(dstatus, DMS_ERR_ARG);
-      return -1;
-    }
-    const int c1 = cTetC[k][0], c2 = cTetC[k][1];
-    int n1, n2, step = 0, sg = 0;
-    switch (code - 1) {
-      case 0:  // omitted the anchor: the other tet sits one step up
-        step = c1;
-        sg = 1;
-        n1 = c2 ^ c1;
-        n2 = 7 ^ c1;
-        break;
-      case 3:  // omitted the top: the other tet sits one step down
-        step = 7 ^ c2;
-        sg = -1;
-        n1 = step;
-        n2 = step | c1;
-        break;
-      case 1:
-        n1 = c2 ^ c1;
-        n2 = c2;
-        break;
-      default:
-        n1 = c1;
-        n2 = c1 | (7 ^ c2);
-        break;
-    }
-    if (sg) {
-      bx += sg * (step & 1);
-      by += sg * ((step >> 1) & 1);
-      bz += sg * ((step >> 2) & 1);
-      if (!fits(D.g, bx, by, bz, 7)) return -1;
-      b += sg * corner_delta(D.g, step);
-    }
-    k = tet_type(n1, n2);
+// Walks with path sharing: every vertex (D0) or non-critical tet (D2) a walk
+// passes is claimed for it (atomicCAS on claim[id]); a walk that reaches an id
+// claimed by another walk stops there, since from there on both follow the
+// same path, and records kLinkBit | that walk instead of an end node.
+constexpr uint32_t kLinkBit = 0x80000000u;
+constexpr uint32_t kUnclaimed = 0xFFFFFFFFu;
+
+__device__ __forceinline__ int64_t dir_find_fwd(const int64_t* list, const uint32_t* start,
+                                                int shift, int64_t id);
+
+// the node a walk ends at, following the walks it joined
+__device__ __forceinline__ uint32_t resolve_walk(const uint32_t* __restrict__ ta,
+                                                 const uint32_t* __restrict__ tb, uint32_t x,
+                                                 int64_t nwalks, int32_t* dstatus) {
+  for (int64_t it = 0; (x & kLinkBit) && it <= nwalks; ++it) {
+    const uint32_t w = x & ~kLinkBit;
+    x = (w & 1) ? tb[w >> 1] : ta[w >> 1];
   }
-  set_status(dstatus, DMS_ERR_TIMEOUT);
-  return -1;
+  if (x & kLinkBit) {
+    set_status(dstatus, DMS_ERR_TIMEOUT);
+    return 0;
+  }
+  return x;
 }
 
 __device__ __forceinline__ int64_t bsearch(const int64_t* __restrict__ a, int64_t lo, int64_t hi,
@@ -215,9 +177,10 @@ __global__ void build_dir(const int64_t* __restrict__ list, int64_t n, int shift
   start[b] = (uint32_t)lo;
 }
 
-__device__ __forceinline__ int64_t dir_find(const Dir& d, int64_t id) {
-  const int64_t b = id >> d.shift;
-  return bsearch(d.list, __ldg(d.start + b), __ldg(d.start + b + 1), id);
+__device__ __forceinline__ int64_t dir_find_fwd(const int64_t* list, const uint32_t* start,
+                                                int shift, int64_t id) {
+  const int64_t b = id >> shift;
+  return bsearch(list, __ldg(start + b), __ldg(start + b + 1), id);
 }
 
 inline int dir_shift(int64_t max_id) {
@@ -241,10 +204,9 @@ struct Tri {
   uint32_t *na, *nb, *ra, *rb, *res;
 };
 
-__global__ void d0_triplets(Dev D, const uint32_t* __restrict__ order,
-                            const uint8_t* __restrict__ desc, const Dir dir0,
-                            const int64_t* __restrict__ crit1, int64_t ne, Tri T,
-                            uint32_t* live, unsigned int* live_n, int32_t* dstatus) {
+// D0: the weight of each critical edge (its lexicographic key).
+__global__ void d0_weights(Dev D, const uint32_t* __restrict__ order,
+                           const int64_t* __restrict__ crit1, int64_t ne, Tri T) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= ne) return;
   int64_t id = crit1[i];
@@ -256,29 +218,43 @@ __global__ void d0_triplets(Dev D, const uint32_t* __restrict__ order,
   uint32_t r = local_rank(D, order, top, oa > ob ? ob : oa);
   T.w[i] = ((uint64_t)(oa > ob ? oa : ob) << 4) | r;
   T.res[i] = kNone;
-  int64_t t0 = descend(D, desc, a, dstatus), t1 = descend(D, desc, b, dstatus);
-  if (t0 == t1) return;
-  int64_t n0 = dir_find(dir0, t0), n1 = dir_find(dir0, t1);
-  if (n0 < 0 || n1 < 0) {
-    set_status(dstatus, DMS_ERR_ARG);
-    return;
-  }
-  T.na[i] = (uint32_t)n0;
-  T.nb[i] = (uint32_t)n1;
-  append(live, live_n, (uint32_t)i);
 }
 
-__global__ void d2_triplets(Dev D, const uint32_t* __restrict__ order,
-                            const uint64_t* __restrict__ rec, const Dir dir3,
-                            const int64_t* __restrict__ crit2, int64_t nt, Tri T,
-                            uint32_t* live, unsigned int* live_n, int32_t* dstatus) {
+// The two cofacets of critical triangle id (anchor a, type k) in field g
+// (anchor coordinates ax, ay, az); -1 where a cofacet leaves the grid.
+__device__ __forceinline__ void tri_cofacets(const Grid& g, int64_t a, int k, int64_t ax,
+                                             int64_t ay, int64_t az, int64_t cof[2]) {
+  const int p = cTriPQ[k][0], q = cTriPQ[k][1];
+  cof[0] = cof[1] = -1;
+  if (q == 7) {
+    const int e = (__popc(p) == 1) ? (7 ^ p) : p;
+    const int e1 = e & -e, e2 = e ^ e1;
+    if (fits(g, ax, ay, az, 7)) {
+      if (__popc(p) == 1) {
+        cof[0] = a * 6 + tet_type(p, p | e1);
+        cof[1] = a * 6 + tet_type(p, p | e2);
+      } else {
+        cof[0] = a * 6 + tet_type(e1, p);
+        cof[1] = a * 6 + tet_type(e2, p);
+      }
+    }
+  } else {
+    if (fits(g, ax, ay, az, 7)) cof[0] = a * 6 + tet_type(p, q);
+    const int e = 7 ^ q;
+    const int64_t bx = ax - (e & 1), by = ay - ((e >> 1) & 1), bz = az - ((e >> 2) & 1);
+    if (fits(g, bx, by, bz, 7)) cof[1] = (a - corner_delta(g, e)) * 6 + tet_type(e, e | p);
+  }
+}
+
+// D2: the weight of each critical triangle (decreasing triangle key).
+__global__ void d2_weights(Dev D, const uint32_t* __restrict__ order,
+                           const int64_t* __restrict__ crit2, int64_t nt, Tri T) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= nt) return;
   int64_t id = crit2[i];
   int64_t a = id / 12;
   int k = (int)(id - a * 12);
   const int p = cTriPQ[k][0], q = cTriPQ[k][1];
-  // weight: decreasing triangle key
   int64_t v[3] = {a, a + corner_delta(D.g, p), a + corner_delta(D.g, q)};
   uint32_t o[3] = {__ldg(order + v[0]), __ldg(order + v[1]), __ldg(order + v[2])};
   int it = 0;
@@ -295,46 +271,213 @@ __global__ void d2_triplets(Dev D, const uint32_t* __restrict__ order,
   uint64_t key = ((uint64_t)o[it] << 8) | (rm << 4) | rl;
   T.w[i] = kMask44 - key;
   T.res[i] = kNone;
-  // the two cofacets
-  int64_t ax, ay, az;
-  xyz(D.g, a, ax, ay, az);
-  int64_t cof[2] = {-1, -1};
-  if (q == 7) {
-    int e = (__popc(p) == 1) ? (7 ^ p) : p;
-    int e1 = e & -e, e2 = e ^ e1;
-    if (fits(D.g, ax, ay, az, 7)) {
-      if (__popc(p) == 1) {
-        cof[0] = a * 6 + tet_type(p, p | e1);
-        cof[1] = a * 6 + tet_type(p, p | e2);
-      } else {
-        cof[0] = a * 6 + tet_type(e1, p);
-        cof[1] = a * 6 + tet_type(e2, p);
-      }
-    }
-  } else {
-    if (fits(D.g, ax, ay, az, 7)) cof[0] = a * 6 + tet_type(p, q);
-    int e = 7 ^ q;
-    int64_t bx = ax - (e & 1), by = ay - ((e >> 1) & 1), bz = az - ((e >> 2) & 1);
-    if (fits(D.g, bx, by, bz, 7)) cof[1] = (bx + D.g.nx * (by + D.g.ny * bz)) * 6 + tet_type(e, e | p);
+}
+
+// ---------------------------------------------------------------------------
+// v-path walks.  Each saddle owns two walks (2s and 2s + 1); a walk's result
+// (its end node, or kLinkBit | the walk it joined) goes to T.ra / T.rb.  A
+// walk policy gives the start of a walk and one step of it.
+// ---------------------------------------------------------------------------
+
+// one field for the whole call
+struct OneField {
+  Grid g;
+  __device__ __forceinline__ void get(int64_t, Grid& out, int64_t& off) const {
+    out = g;
+    off = 0;
   }
-  int64_t end[2];
-  for (int j = 0; j < 2; ++j) end[j] = cof[j] < 0 ? -1 : ascend(D, rec, cof[j], dstatus);
-  if (end[0] == end[1]) return;
-  int64_t node[2];
-  for (int j = 0; j < 2; ++j) {
-    if (end[j] < 0) {
-      node[j] = 0;
-    } else {
-      int64_t pos = dir_find(dir3, end[j]);
-      if (pos < 0) {
-        set_status(dstatus, DMS_ERR_ARG);
-        return;
+};
+
+// a batch: the field that holds an anchor, by binary search of the table
+struct ManyFields {
+  const dms_field_desc* fd;
+  int n;
+  __device__ __forceinline__ void get(int64_t anchor, Grid& out, int64_t& off) const {
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (fd[mid].offset <= anchor) lo = mid;
+      else hi = mid;
+    }
+    const dms_field_desc d = fd[lo];
+    out.nx = d.nx;
+    out.ny = d.ny;
+    out.nz = d.nz;
+    out.sxy = (int64_t)d.nx * d.ny;
+    out.n = out.sxy * d.nz;
+    off = d.offset;
+  }
+};
+
+__device__ __forceinline__ int64_t slot_delta_g(const Grid& g, int s) {
+  const int c = (0x7653421 >> (4 * (s < 7 ? s : s - 7))) & 15;
+  const int64_t d = (c & 1) + ((c >> 1) & 1) * g.nx + ((c >> 2) & 1) * g.sxy;
+  return s < 7 ? d : -d;
+}
+
+// D0: descending paths from the two vertices of a critical edge to minima
+template <class F>
+struct DescWalk {
+  F fields;
+  const int64_t* crit1;
+  const uint8_t* desc;
+  Dir dir0;
+  uint32_t* claim;
+  struct State {
+    Grid g;
+    int64_t v, it;
+  };
+  // start walk j of saddle s; false if it has already ended (never, here)
+  __device__ __forceinline__ bool start(int64_t s, int j, State& st, uint32_t& r) const {
+    const int64_t id = crit1[s];
+    const int64_t a = id / 7;
+    const int k = (int)(id - a * 7);
+    int64_t off;
+    fields.get(a, st.g, off);
+    st.v = j ? a + corner_delta(st.g, cCornerOfEdge[k]) : a;
+    st.it = 0;
+    (void)r;
+    return true;
+  }
+  // one step; false when the walk has ended with result r
+  __device__ __forceinline__ bool step(State& st, uint32_t w, uint32_t& r,
+                                       int32_t* dstatus) const {
+    const uint8_t d = __ldg(desc + st.v);
+    if (d >= 14) {
+      const int64_t pos = dir_find_fwd(dir0.list, dir0.start, dir0.shift, st.v);
+      if (pos < 0) set_status(dstatus, DMS_ERR_ARG);
+      r = pos < 0 ? 0u : (uint32_t)pos;
+      return false;
+    }
+    const uint32_t old = atomicCAS(claim + st.v, kUnclaimed, w);
+    if (old != kUnclaimed) {
+      r = kLinkBit | old;
+      return false;
+    }
+    st.v += slot_delta_g(st.g, d);
+    if (++st.it > st.g.n) {
+      set_status(dstatus, DMS_ERR_TIMEOUT);
+      r = 0;
+      return false;
+    }
+    return true;
+  }
+};
+
+// D2: ascending dual paths from the two cofacets of a critical triangle to a
+// critical tetrahedron (node j + 1) or out of the grid (node 0, OUTSIDE)
+template <class F>
+struct DualWalk {
+  F fields;
+  const int64_t* crit2;
+  const uint64_t* rec;
+  Dir dir3;
+  uint32_t* claim;
+  struct State {
+    Grid g;
+    int64_t b, bx, by, bz, it;
+    int k;
+  };
+  __device__ __forceinline__ bool start(int64_t s, int j, State& st, uint32_t& r) const {
+    const int64_t id = crit2[s];
+    const int64_t a = id / 12;
+    const int k = (int)(id - a * 12);
+    int64_t off;
+    fields.get(a, st.g, off);
+    int64_t ax, ay, az;
+    xyz(st.g, a - off, ax, ay, az);
+    int64_t cof[2];
+    tri_cofacets(st.g, a, k, ax, ay, az, cof);
+    const int64_t t = cof[j];
+    if (t < 0) {
+      r = 0;  // no cofacet on that side: the walk starts OUTSIDE
+      return false;
+    }
+    st.b = t / 6;
+    st.k = (int)(t - st.b * 6);
+    xyz(st.g, st.b - off, st.bx, st.by, st.bz);
+    st.it = 0;
+    return true;
+  }
+  __device__ __forceinline__ bool step(State& st, uint32_t w, uint32_t& r,
+                                       int32_t* dstatus) const {
+    const uint32_t code = (uint32_t)(__ldg(rec + st.b) >> (33 + 3 * st.k)) & 7u;
+    if (code == 7u) {
+      const int64_t pos = dir_find_fwd(dir3.list, dir3.start, dir3.shift, st.b * 6 + st.k);
+      if (pos < 0) set_status(dstatus, DMS_ERR_ARG);
+      r = pos < 0 ? 0u : (uint32_t)pos + 1;
+      return false;
+    }
+    if (code < 1u || code > 4u) {
+      set_status(dstatus, DMS_ERR_ARG);
+      r = 0;
+      return false;
+    }
+    const uint32_t old = atomicCAS(claim + st.b * 6 + st.k, kUnclaimed, w);
+    if (old != kUnclaimed) {
+      r = kLinkBit | old;
+      return false;
+    }
+    const int c1 = cTetC[st.k][0], c2 = cTetC[st.k][1];
+    int n1, n2, stp = 0, sg = 0;
+    switch (code - 1) {
+      case 0: stp = c1; sg = 1; n1 = c2 ^ c1; n2 = 7 ^ c1; break;    // omits the anchor
+      case 3: stp = 7 ^ c2; sg = -1; n1 = stp; n2 = stp | c1; break;  // omits the top
+      case 1: n1 = c2 ^ c1; n2 = c2; break;
+      default: n1 = c1; n2 = c1 | (7 ^ c2); break;
+    }
+    if (sg) {
+      st.bx += sg * (stp & 1);
+      st.by += sg * ((stp >> 1) & 1);
+      st.bz += sg * ((stp >> 2) & 1);
+      if (!fits(st.g, st.bx, st.by, st.bz, 7)) {
+        r = 0;  // left the grid: OUTSIDE
+        return false;
       }
-      node[j] = pos + 1;
+      st.b += sg * corner_delta(st.g, stp);
+    }
+    st.k = tet_type(n1, n2);
+    if (++st.it > 6 * st.g.n) {
+      set_status(dstatus, DMS_ERR_TIMEOUT);
+      r = 0;
+      return false;
+    }
+    return true;
+  }
+};
+
+// Both walks of every saddle, one thread per saddle (grid-stride when the
+// count is on the device).  The walks are chains of dependent loads; many
+// resident warps hide their latency, and path sharing keeps them short.
+template <class W>
+__global__ void __launch_bounds__(256) walk_each(const W wk, const int64_t* n_dev, int64_t n_host,
+                                                 Tri T, int32_t* dstatus) {
+  const int64_t ns = n_dev ? *n_dev : n_host;
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < ns;
+       s += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll 1
+    for (int j = 0; j < 2; ++j) {
+      typename W::State st;
+      uint32_t r = 0;
+      if (wk.start(s, j, st, r))
+        while (wk.step(st, (uint32_t)(2 * s + j), r, dstatus)) {
+        }
+      (j ? T.rb : T.ra)[s] = r;
     }
   }
-  T.na[i] = (uint32_t)node[0];
-  T.nb[i] = (uint32_t)node[1];
+}
+
+// Second pass (D0 and D2): resolve both walks of each saddle to their end
+// nodes; a saddle whose walks end at different nodes is live in the pairing.
+__global__ void link_walks(int64_t nt, Tri T, uint32_t* live, unsigned int* live_n,
+                        int32_t* dstatus) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nt) return;
+  const uint32_t n0 = resolve_walk(T.ra, T.rb, T.ra[i], 2 * nt, dstatus);
+  const uint32_t n1 = resolve_walk(T.ra, T.rb, T.rb[i], 2 * nt, dstatus);
+  if (n0 == n1) return;
+  T.na[i] = n0;
+  T.nb[i] = n1;
   append(live, live_n, (uint32_t)i);
 }
 
@@ -398,7 +541,9 @@ __global__ void round_find(const uint32_t* __restrict__ live, const unsigned int
   unsigned int n = *live_n;
   for (unsigned int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     uint32_t i = live[j];
-    uint32_t a = find_root(parent, T.na[i]), b = find_root(parent, T.nb[i]);
+    // roots only ever gain parents: search from last round's roots
+    uint32_t a = find_root(parent, round == 1 ? T.na[i] : T.ra[i]);
+    uint32_t b = find_root(parent, round == 1 ? T.nb[i] : T.rb[i]);
     T.ra[i] = a;
     T.rb[i] = b;
     if (a == b) continue;
@@ -607,11 +752,13 @@ struct DiagWs {
   unsigned long long* best;
   uint64_t* age;
   uint32_t* dir;  // kDirBuckets + 1 bucket starts
+  uint32_t* claim;  // one word per tet id: the dual walk that passed it
+  int64_t nclaim;
   radix64::Buffers rb;
   size_t bytes;
 };
 
-DiagWs carve_diag(void* base, const int64_t* nc) {
+DiagWs carve_diag(void* base, const int64_t* nc, int64_t nvert) {
   WsCarver c(base);
   DiagWs w;
   const int64_t nsad = std::max<int64_t>(std::max<int64_t>(nc[1], nc[2]), 1);
@@ -633,6 +780,8 @@ DiagWs carve_diag(void* base, const int64_t* nc) {
   w.best = c.take<unsigned long long>(nnode);
   w.age = c.take<uint64_t>(nnode);
   w.dir = c.take<uint32_t>(kDirBuckets + 1);
+  w.nclaim = 6 * nvert;
+  w.claim = c.take<uint32_t>(w.nclaim);
   w.rb = radix64::carve(c, std::max<int64_t>(nsad, 4096));
   w.bytes = c.used;
   return w;
@@ -692,8 +841,7 @@ int write_diagram(int dim, DiagWs& w, const Dev& D, const float* f, const uint32
 }  // namespace
 
 size_t diagram_workspace_bytes(const Grid& g, const int64_t* n_crit) {
-  (void)g;
-  return carve_diag(nullptr, n_crit).bytes;
+  return carve_diag(nullptr, n_crit, g.n).bytes;
 }
 
 int launch_diagram(const float* f, const uint32_t* order, const uint8_t* desc, const uint64_t* rec,
@@ -701,7 +849,7 @@ int launch_diagram(const float* f, const uint32_t* order, const uint8_t* desc, c
                    const int64_t* crit3, const int64_t* nc, dms_pair* d0, int64_t cap0,
                    dms_pair* d2, int64_t cap2, dms_pair* ess, int64_t* n_out, void* ws,
                    int32_t* dstatus, cudaStream_t s) {
-  DiagWs w = carve_diag(ws, nc);
+  DiagWs w = carve_diag(ws, nc, g.n);
   Dev D;
   D.g = g;
   for (int sl = 0; sl < 14; ++sl) {
@@ -721,8 +869,11 @@ int launch_diagram(const float* f, const uint32_t* order, const uint8_t* desc, c
   if (nc[1] > 0) {
     Dir d0dir{crit0, nc[0], w.dir, dir_shift(g.n)};
     build_dir<<<nb(kDirBuckets + 1), TB, 0, s>>>(crit0, nc[0], d0dir.shift, w.dir); count_launch();
-    d0_triplets<<<nb(nc[1]), TB, 0, s>>>(D, order, desc, d0dir, crit1, nc[1], w.T0, w.live0,
-                                         w.ctr + 0, dstatus); count_launch();
+    DMS_CUDA_OK(cudaMemsetAsync(w.claim, 0xFF, g.n * sizeof(uint32_t), s));
+    d0_weights<<<nb(nc[1]), TB, 0, s>>>(D, order, crit1, nc[1], w.T0); count_launch();
+    const DescWalk<OneField> wk{OneField{g}, crit1, desc, d0dir, w.claim};
+    walk_each<<<nb(nc[1]), TB, 0, s>>>(wk, nullptr, nc[1], w.T0, dstatus); count_launch();
+    link_walks<<<nb(nc[1]), TB, 0, s>>>(nc[1], w.T0, w.live0, w.ctr + 0, dstatus); count_launch();
   }
   int st = run_rounds(w, w.T0, s, dstatus);
   if (st) return st;
@@ -735,8 +886,11 @@ int launch_diagram(const float* f, const uint32_t* order, const uint8_t* desc, c
   if (nc[2] > 0) {
     Dir d3dir{crit3, nc[3], w.dir, dir_shift(6 * g.n)};
     build_dir<<<nb(kDirBuckets + 1), TB, 0, s>>>(crit3, nc[3], d3dir.shift, w.dir); count_launch();
-    d2_triplets<<<nb(nc[2]), TB, 0, s>>>(D, order, rec, d3dir, crit2, nc[2], w.T2, w.live0,
-                                         w.ctr + 0, dstatus); count_launch();
+    DMS_CUDA_OK(cudaMemsetAsync(w.claim, 0xFF, w.nclaim * sizeof(uint32_t), s));
+    d2_weights<<<nb(nc[2]), TB, 0, s>>>(D, order, crit2, nc[2], w.T2); count_launch();
+    const DualWalk<OneField> wk{OneField{g}, crit2, rec, d3dir, w.claim};
+    walk_each<<<nb(nc[2]), TB, 0, s>>>(wk, nullptr, nc[2], w.T2, dstatus); count_launch();
+    link_walks<<<nb(nc[2]), TB, 0, s>>>(nc[2], w.T2, w.live0, w.ctr + 0, dstatus); count_launch();
   }
   st = run_rounds(w, w.T2, s, dstatus);
   if (st) return st;
@@ -809,53 +963,6 @@ __device__ __forceinline__ uint32_t local_rank_f(const Grid& g, int64_t off,
   return r;
 }
 
-__device__ __forceinline__ int64_t descend_f(const Grid& g, const uint8_t* __restrict__ desc,
-                                             int64_t v, int32_t* dstatus) {
-  for (int64_t it = 0; it < g.n; ++it) {
-    const uint8_t d = __ldg(desc + v);
-    if (d >= 14) return v;
-    v += slot_delta_of(g, d);
-  }
-  set_status(dstatus, DMS_ERR_TIMEOUT);
-  return v;
-}
-
-// global tet id t in field (g, off); -1 = OUTSIDE
-__device__ __forceinline__ int64_t ascend_f(const Grid& g, int64_t off,
-                                            const uint64_t* __restrict__ rec, int64_t t,
-                                            int32_t* dstatus) {
-  int64_t b = t / 6;
-  int k = (int)(t - b * 6);
-  int64_t bx, by, bz;
-  xyz(g, b - off, bx, by, bz);
-  for (int64_t it = 0; it < 6 * g.n; ++it) {
-    const uint32_t code = (uint32_t)(__ldg(rec + b) >> (33 + 3 * k)) & 7u;
-    if (code == 7u) return b * 6 + k;
-    if (code < 1u || code > 4u) {
-      set_status(dstatus, DMS_ERR_ARG);
-      return -1;
-    }
-    const int c1 = cTetC[k][0], c2 = cTetC[k][1];
-    int n1, n2, step = 0, sg = 0;
-    switch (code - 1) {
-      case 0: step = c1; sg = 1; n1 = c2 ^ c1; n2 = 7 ^ c1; break;
-      case 3: step = 7 ^ c2; sg = -1; n1 = step; n2 = step | c1; break;
-      case 1: n1 = c2 ^ c1; n2 = c2; break;
-      default: n1 = c1; n2 = c1 | (7 ^ c2); break;
-    }
-    if (sg) {
-      bx += sg * (step & 1);
-      by += sg * ((step >> 1) & 1);
-      bz += sg * ((step >> 2) & 1);
-      if (!fits(g, bx, by, bz, 7)) return -1;
-      b += sg * corner_delta(g, step);
-    }
-    k = tet_type(n1, n2);
-  }
-  set_status(dstatus, DMS_ERR_TIMEOUT);
-  return -1;
-}
-
 __global__ void b_build_dir(const int64_t* __restrict__ list, const int64_t* __restrict__ n_dev,
                             int shift, uint32_t* start) {
   const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -903,10 +1010,9 @@ __global__ void b_essential(const FieldTab ft, const float* __restrict__ f,
   }
 }
 
-__global__ void b_d0_triplets(const FieldTab ft, const uint32_t* __restrict__ order,
-                              const uint8_t* __restrict__ desc, const Dir dir0,
-                              const int64_t* __restrict__ crit1, const int64_t* __restrict__ cnt,
-                              Tri T, uint32_t* live, unsigned int* live_n, int32_t* dstatus) {
+__global__ void b_d0_weights(const FieldTab ft, const uint32_t* __restrict__ order,
+                             const int64_t* __restrict__ crit1, const int64_t* __restrict__ cnt,
+                             Tri T) {
   const int64_t ne = cnt[1];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ne;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -921,16 +1027,6 @@ __global__ void b_d0_triplets(const FieldTab ft, const uint32_t* __restrict__ or
     const uint32_t r = local_rank_f(g, fd.offset, order, top, oa > ob ? ob : oa);
     T.w[i] = ((uint64_t)(oa > ob ? oa : ob) << 4) | r;
     T.res[i] = kNone;
-    const int64_t t0 = descend_f(g, desc, a, dstatus), t1 = descend_f(g, desc, b, dstatus);
-    if (t0 == t1) continue;
-    const int64_t n0 = dir_find(dir0, t0), n1 = dir_find(dir0, t1);
-    if (n0 < 0 || n1 < 0) {
-      set_status(dstatus, DMS_ERR_ARG);
-      continue;
-    }
-    T.na[i] = (uint32_t)n0;
-    T.nb[i] = (uint32_t)n1;
-    append(live, live_n, (uint32_t)i);
   }
 }
 
@@ -971,10 +1067,9 @@ __global__ void b_init_nodes_d2(const FieldTab ft, const uint32_t* __restrict__ 
   }
 }
 
-__global__ void b_d2_triplets(const FieldTab ft, const uint32_t* __restrict__ order,
-                              const uint64_t* __restrict__ rec, const Dir dir3,
-                              const int64_t* __restrict__ crit2, const int64_t* __restrict__ cnt,
-                              Tri T, uint32_t* live, unsigned int* live_n, int32_t* dstatus) {
+__global__ void b_d2_weights(const FieldTab ft, const uint32_t* __restrict__ order,
+                             const int64_t* __restrict__ crit2, const int64_t* __restrict__ cnt,
+                             Tri T) {
   const int64_t nt = cnt[2];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nt;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -1000,47 +1095,19 @@ __global__ void b_d2_triplets(const FieldTab ft, const uint32_t* __restrict__ or
     const uint64_t key = ((uint64_t)o[it] << 8) | (rm << 4) | rl;
     T.w[i] = kMask44 - key;
     T.res[i] = kNone;
-    int64_t ax, ay, az;
-    xyz(g, a - fd.offset, ax, ay, az);
-    int64_t cof[2] = {-1, -1};
-    if (q == 7) {
-      const int e = (__popc(p) == 1) ? (7 ^ p) : p;
-      const int e1 = e & -e, e2 = e ^ e1;
-      if (fits(g, ax, ay, az, 7)) {
-        if (__popc(p) == 1) {
-          cof[0] = a * 6 + tet_type(p, p | e1);
-          cof[1] = a * 6 + tet_type(p, p | e2);
-        } else {
-          cof[0] = a * 6 + tet_type(e1, p);
-          cof[1] = a * 6 + tet_type(e2, p);
-        }
-      }
-    } else {
-      if (fits(g, ax, ay, az, 7)) cof[0] = a * 6 + tet_type(p, q);
-      const int e = 7 ^ q;
-      const int64_t bx = ax - (e & 1), by = ay - ((e >> 1) & 1), bz = az - ((e >> 2) & 1);
-      if (fits(g, bx, by, bz, 7)) cof[1] = (a - corner_delta(g, e)) * 6 + tet_type(e, e | p);
-    }
-    int64_t end[2];
-    for (int j = 0; j < 2; ++j) end[j] = cof[j] < 0 ? -1 : ascend_f(g, fd.offset, rec, cof[j], dstatus);
-    if (end[0] == end[1]) continue;
-    int64_t node[2];
-    bool ok = true;
-    for (int j = 0; j < 2; ++j) {
-      if (end[j] < 0) {
-        node[j] = 0;
-      } else {
-        const int64_t pos = dir_find(dir3, end[j]);
-        if (pos < 0) ok = false;
-        node[j] = pos + 1;
-      }
-    }
-    if (!ok) {
-      set_status(dstatus, DMS_ERR_ARG);
-      continue;
-    }
-    T.na[i] = (uint32_t)node[0];
-    T.nb[i] = (uint32_t)node[1];
+  }
+}
+
+__global__ void b_link_walks(const int64_t* __restrict__ n_dev, Tri T, uint32_t* live,
+                             unsigned int* live_n, int32_t* dstatus) {
+  const int64_t nt = *n_dev;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nt;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t n0 = resolve_walk(T.ra, T.rb, T.ra[i], 2 * nt, dstatus);
+    const uint32_t n1 = resolve_walk(T.ra, T.rb, T.rb[i], 2 * nt, dstatus);
+    if (n0 == n1) continue;
+    T.na[i] = n0;
+    T.nb[i] = n1;
     append(live, live_n, (uint32_t)i);
   }
 }
@@ -1205,9 +1272,9 @@ int diagram_batch_rounds() { return kBatchRounds; }
 
 // Workspace of the batched pairing: the DiagWs of the capacities plus the
 // per-field counters and pair-tile sums.
-size_t diagram_batch_workspace_bytes(int64_t nfields, const int64_t* caps) {
+size_t diagram_batch_workspace_bytes(int64_t nfields, const int64_t* caps, int64_t total) {
   WsCarver c(nullptr);
-  c.take<unsigned char>(carve_diag(nullptr, caps).bytes);
+  c.take<unsigned char>(carve_diag(nullptr, caps, total).bytes);
   const int64_t nsad = std::max<int64_t>(std::max<int64_t>(caps[1], caps[2]), 1);
   const int64_t ntiles = (nsad + PTILE - 1) / PTILE;
   c.take<unsigned long long>(2 * (nfields + 1));
@@ -1223,8 +1290,8 @@ int launch_diagram_batch(const float* f, const uint32_t* order, const uint8_t* d
                          int64_t* pair_offsets, dms_pair* ess, int64_t* pair_totals, void* ws,
                          int32_t* dstatus, cudaStream_t s) {
   WsCarver c(ws);
-  unsigned char* dbase = c.take<unsigned char>(carve_diag(nullptr, caps).bytes);
-  DiagWs w = carve_diag(dbase, caps);
+  unsigned char* dbase = c.take<unsigned char>(carve_diag(nullptr, caps, total_vertices).bytes);
+  DiagWs w = carve_diag(dbase, caps, total_vertices);
   const int64_t nsad = std::max<int64_t>(std::max<int64_t>(caps[1], caps[2]), 1);
   const int64_t ntiles = (nsad + PTILE - 1) / PTILE;
   unsigned long long* fcount = c.take<unsigned long long>(2 * (nfields + 1));
@@ -1270,8 +1337,13 @@ int launch_diagram_batch(const float* f, const uint32_t* order, const uint8_t* d
   b_essential<<<G, TB, 0, s>>>(ft, f, order, crit[0], cnt_dev, ess); count_launch();
   b_build_dir<<<dir_blocks, TB, 0, s>>>(crit[0], cnt_dev + 0, shift0, w.dir); count_launch();
   const Dir dir0{crit[0], caps[0], w.dir, shift0};
-  b_d0_triplets<<<G, TB, 0, s>>>(ft, order, desc, dir0, crit[1], cnt_dev, w.T0, w.live0, w.ctr + 0,
-                                 dstatus); count_launch();
+  DMS_CUDA_OK(cudaMemsetAsync(w.claim, 0xFF, total_vertices * sizeof(uint32_t), s));
+  b_d0_weights<<<G, TB, 0, s>>>(ft, order, crit[1], cnt_dev, w.T0); count_launch();
+  {
+    const DescWalk<ManyFields> wk{ManyFields{fields_dev, nfields}, crit[1], desc, dir0, w.claim};
+    walk_each<<<G * 2, TB, 0, s>>>(wk, cnt_dev + 1, 0, w.T0, dstatus); count_launch();
+  }
+  b_link_walks<<<G, TB, 0, s>>>(cnt_dev + 1, w.T0, w.live0, w.ctr + 0, dstatus); count_launch();
   rounds(w.T0);
   write(0, w.T0, crit[0], crit[1], cnt_dev + 1, d0, pair_offsets, pair_totals + 0, fcount);
 
@@ -1280,8 +1352,13 @@ int launch_diagram_batch(const float* f, const uint32_t* order, const uint8_t* d
   b_init_nodes_d2<<<G, TB, 0, s>>>(ft, order, crit[3], cnt_dev, w.parent, w.best, w.age); count_launch();
   b_build_dir<<<dir_blocks, TB, 0, s>>>(crit[3], cnt_dev + 3, shift3, w.dir); count_launch();
   const Dir dir3{crit[3], caps[3], w.dir, shift3};
-  b_d2_triplets<<<G, TB, 0, s>>>(ft, order, rec, dir3, crit[2], cnt_dev, w.T2, w.live0, w.ctr + 0,
-                                 dstatus); count_launch();
+  DMS_CUDA_OK(cudaMemsetAsync(w.claim, 0xFF, w.nclaim * sizeof(uint32_t), s));
+  b_d2_weights<<<G, TB, 0, s>>>(ft, order, crit[2], cnt_dev, w.T2); count_launch();
+  {
+    const DualWalk<ManyFields> wk{ManyFields{fields_dev, nfields}, crit[2], rec, dir3, w.claim};
+    walk_each<<<G * 2, TB, 0, s>>>(wk, cnt_dev + 2, 0, w.T2, dstatus); count_launch();
+  }
+  b_link_walks<<<G, TB, 0, s>>>(cnt_dev + 2, w.T2, w.live0, w.ctr + 0, dstatus); count_launch();
   rounds(w.T2);
   write(2, w.T2, crit[2], crit[3], cnt_dev + 2, d2, pair_offsets + (nfields + 1), pair_totals + 1,
         fcount + (nfields + 1));

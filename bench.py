@@ -49,12 +49,26 @@ def make_field(workload: str, n: int, device, seed=0):
 
 
 def load_peaks():
+    """(HBM GB/s, max SM MHz, which): the measured copy bandwidth and clock of
+    this GPU pool, else the fallback figures."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         with open(p) as fh:
             d = json.load(fh)
-        return float(d["hbm_gbs"]), "measured"
-    return 6800.0, "fallback"
+        return float(d["hbm_gbs"]), float(d.get("sm_max_mhz", 2070.0)), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+# The gradient kernel is bound by integer instruction issue, not by HBM (it
+# moves 13 B per vertex but executes ~240 warp instructions per vertex).  Its
+# roofline is the issue rate: SMs x 4 schedulers x 32 lanes x SM clock.  The
+# per-vertex figures below are those of the current kernel, from one ncu
+# capture of gradient_kernel on the same field recipe at 384^3 (profiles/
+# gradient_kernel_c3.md): smsp__inst_executed.sum / vertices, and
+# (dram__bytes_read.sum + dram__bytes_write.sum) / vertices.
+GRAD_WARP_INST_PER_VERTEX = 238.38
+GRAD_DRAM_BYTES_PER_VERTEX = 12.30
+GRAD_ALGO_BYTES_PER_VERTEX = 4 + 8 + 1  # read order, write record and desc
 
 
 class ClockSampler:
@@ -124,6 +138,91 @@ def cpu_baseline(field_np: np.ndarray, crop: int):
                       f"of the workload field, {dt:.1f} s"}
 
 
+def bench_batched(dev, steps: int, warmup: int):
+    """256 fields of uneven dims (each axis U{32..256}; even fields Gaussian
+    mixtures, odd fields U[0,1)), all resident in HBM: one batched launch
+    replayed from a CUDA graph against the same fields run one by one
+    through the single-field calls."""
+    import torch
+    from paper_2505_21266_gb300 import batch as B
+    from paper_2505_21266_gb300 import fields
+    shapes = fields.batch_shapes(256, 32, 256, seed=0)
+    xs = [fields.batch_field(i, s, seed=0, device=dev) for i, s in enumerate(shapes)]
+    total = int(sum(a * b * c for a, b, c in shapes))
+    variant = B.autotune(shapes, dev, fields=xs)
+    b = B.Batch(shapes, dev, tile_variant=variant)
+    b.set_fields(xs)
+    b.capture()
+    for _ in range(warmup):
+        b.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        b.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    b.check()
+    batched_ms = e0.elapsed_time(e1) / steps
+    del b
+    torch.cuda.empty_cache()
+    B.per_field(xs)  # warm-up
+    torch.cuda.synchronize()
+    e0.record()
+    reps = max(1, min(steps, 2))
+    for _ in range(reps):
+        B.per_field(xs)
+    e1.record()
+    torch.cuda.synchronize()
+    per_ms = e0.elapsed_time(e1) / reps
+    del xs
+    torch.cuda.empty_cache()
+    return {"workload": "256 fields, axes U{32..256}, half Gaussian mixtures (16, sigma "
+                        "U[0.05,0.2]) + U[0,1e-3), half U[0,1)",
+            "fields": 256, "vertices": total, "tile_variant": variant,
+            "batched_ms": batched_ms, "batched_fields_per_s": 256 / (batched_ms / 1e3),
+            "batched_vertices_per_s": total / (batched_ms / 1e3),
+            "per_field_ms": per_ms, "per_field_fields_per_s": 256 / (per_ms / 1e3),
+            "speedup": per_ms / batched_ms, "graph": True}
+
+
+def bench_differentiable(dev, steps: int, warmup: int):
+    """128^3 field (32 Gaussians + U[0,1e-4)): one gradient-descent step on
+    the topological loss (diagram, loss, backward kernel, update) against the
+    forward-only diagram of the same field."""
+    import torch
+    import paper_2505_21266_gb300 as dms
+    from paper_2505_21266_gb300 import fields
+    f0 = fields.config4(0, dev)
+    x = f0.clone().requires_grad_(True)
+
+    def gd_step():
+        loss = dms.topological_loss(x, 0.05)
+        loss.backward()
+        with torch.no_grad():
+            x.sub_(1e-2 * x.grad)
+            x.grad = None
+        return loss
+
+    def fwd():
+        return dms.diagram(f0)
+
+    out = {}
+    for name, fn in (("forward_ms", fwd), ("gd_step_ms", gd_step)):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            fn()
+        torch.cuda.synchronize()
+        out[name] = (time.perf_counter() - t0) / steps * 1e3
+    out["workload"] = "128^3, 32 Gaussians (sigma U[0.05,0.2]) + U[0,1e-4); loss = sum of " \
+                      "(death - birth)^2 over pairs with persistence < 0.05, lr 1e-2"
+    out["gd_over_forward"] = out["gd_step_ms"] / out["forward_ms"]
+    return out
+
+
 def run_reference(args):
     """--impl reference: the oracle on bounded crops of the workload field."""
     rank = int(os.environ.get("RANK", "0"))
@@ -171,9 +270,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
     ap.add_argument("--size", type=int, default=0, help="override the grid edge length")
-    ap.add_argument("--crop", type=int, default=48, help="oracle crop edge (CPU legs)")
+    ap.add_argument("--crop", type=int, default=80, help="oracle crop edge (CPU legs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 256-field batch leg")
+    ap.add_argument("--no-diff", action="store_true", help="skip the differentiable leg")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -235,7 +336,8 @@ def main():
         return d, st, c
 
     print(f"field ready: {nvert} vertices", file=sys.stderr, flush=True)
-    for _ in range(args.warmup):
+    d, st, c = staged(f)  # the first pass also sizes the capacities
+    for _ in range(args.warmup - 1):
         d, st, c = staged(f)
     torch.cuda.synchronize()
     if int(st.item()) != 0:
@@ -287,9 +389,12 @@ def main():
         e2e = {"value": nvert * world * args.steps / dt, "unit": "vertices/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
-    peak, peak_kind = load_peaks()
-    grad_bytes = nvert * (4 + 8 + 1)  # read order, write record and desc
-    achieved = grad_bytes / (grad_ms / 1e3) / 1e9
+    hbm_peak, sm_mhz, peak_kind = load_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    issue_peak = sms * 4 * 32 * sm_mhz * 1e6 / 1e12  # lane-instructions/s, in T
+    grad_inst = GRAD_WARP_INST_PER_VERTEX * 32 * nvert
+    achieved = grad_inst / (grad_ms / 1e3) / 1e12
+    grad_bytes = GRAD_ALGO_BYTES_PER_VERTEX * nvert
     line = {
         "metric": METRIC, "value": value, "unit": "vertices/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -299,16 +404,28 @@ def main():
                    "l2": "inputs (4 GiB field, 4 GiB order) larger than L2, no flush",
                    "critical": crit_counts, "pairs_d0_d2": n_pairs,
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "hbm", "kernel": "gradient_kernel", "achieved": achieved,
-                     "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "peak_kind": peak_kind, "traffic": None,
-                     "kernel_ms": grad_ms, "algorithmic_bytes": grad_bytes},
+        "roofline": {"bound": "alu", "kernel": "gradient_kernel", "achieved": achieved,
+                     "peak": issue_peak, "unit": "Tinst/s (lane-instructions)",
+                     "frac": achieved / issue_peak,
+                     "peak_kind": f"derived: {sms} SMs x 4 x 32 lanes x {sm_mhz:.0f} MHz",
+                     "traffic": GRAD_DRAM_BYTES_PER_VERTEX * nvert,
+                     "kernel_ms": grad_ms, "warp_inst_per_vertex": GRAD_WARP_INST_PER_VERTEX,
+                     "hbm": {"algorithmic_bytes": grad_bytes,
+                             "achieved_gbs": grad_bytes / (grad_ms / 1e3) / 1e9,
+                             "peak_gbs": hbm_peak, "peak_kind": peak_kind,
+                             "frac": grad_bytes / (grad_ms / 1e3) / 1e9 / hbm_peak}},
         "gpu_launches": launches,
         "clocks": clocks,
         "e2e": e2e,
     }
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(f.cpu().numpy(), args.crop)
+    del f, d, c
+    torch.cuda.empty_cache()
+    if not args.no_batched:
+        line["batched"] = bench_batched(dev, args.steps, args.warmup)
+    if not args.no_diff:
+        line["differentiable"] = bench_differentiable(dev, args.steps, args.warmup)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

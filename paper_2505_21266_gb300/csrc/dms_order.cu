@@ -155,8 +155,7 @@ __global__ void __launch_bounds__(SORT_NT) upsweep_kernel(int pass, const Plan* 
       else if (src != SRC_FIELD) v = __ldg((src == SRC_A ? va : vb) + i);
       d = digit_of(pass, k, v, fl);
     }
-    unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
-    if (d < 256u && lane == __ffs(peers) - 1) h[warp][d] += __popc(peers);
+    if (d < 256u) atomicAdd(&h[warp][d], 1u);  // counts only: no order needed
   }
   __syncthreads();
   for (int d = threadIdx.x; d < 256; d += SORT_NT) {
@@ -262,7 +261,7 @@ struct DownSmem {
   uint32_t sv[SORT_TILE];
 };
 
-__global__ void __launch_bounds__(SORT_NT, 3) downsweep_kernel(
+__global__ void __launch_bounds__(SORT_NT, 4) downsweep_kernel(
     int pass, const Plan* __restrict__ plan, const float* __restrict__ f, uint32_t* ka,
     uint32_t* kb, uint32_t* va, uint32_t* vb, uint32_t* __restrict__ order, const Fields fl,
     int64_t n, int64_t ntiles, const unsigned int* __restrict__ th) {

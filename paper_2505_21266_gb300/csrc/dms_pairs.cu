@@ -48,6 +48,26 @@ __constant__ int cTetC[6][2] = {{1, 3}, {1, 5}, {2, 3}, {2, 6}, {4, 5}, {4, 6}};
 // neighbour slots: +c for s < 7, -c for s >= 7, c = corner of edge type s % 7
 __constant__ int cSlotCorner[14] = {1, 2, 4, 3, 5, 6, 7, 1, 2, 4, 3, 5, 6, 7};
 
+// the union-find nodes (extrema), as separate arrays so that the parent
+// array, which the root searches chase, stays small enough for L2: parent,
+// the tag of the node's lightest live saddle in the current round, its age
+// (a larger age is younger)
+struct Nodes {
+  uint32_t* parent;
+  unsigned long long* best;
+  uint64_t* age;
+};
+
+// one saddle of the pairing, in one 32-byte sector: its weight, its two
+// end nodes, their roots in the current round and the extremum it kills
+struct Sad {
+  uint64_t w;
+  uint32_t na, nb, ra, rb, res, pad;
+};
+struct Tri {
+  Sad* s;
+};
+
 struct Dev {
   Grid g;
   int64_t slot_delta[14];
@@ -126,12 +146,11 @@ __device__ __forceinline__ int64_t dir_find_fwd(const int64_t* list, const uint3
                                                 int shift, int64_t id);
 
 // the node a walk ends at, following the walks it joined
-__device__ __forceinline__ uint32_t resolve_walk(const uint32_t* __restrict__ ta,
-                                                 const uint32_t* __restrict__ tb, uint32_t x,
+__device__ __forceinline__ uint32_t resolve_walk(const Sad* __restrict__ sd, uint32_t x,
                                                  int64_t nwalks, int32_t* dstatus) {
   for (int64_t it = 0; (x & kLinkBit) && it <= nwalks; ++it) {
     const uint32_t w = x & ~kLinkBit;
-    x = (w & 1) ? tb[w >> 1] : ta[w >> 1];
+    x = (w & 1) ? sd[w >> 1].rb : sd[w >> 1].ra;
   }
   if (x & kLinkBit) {
     set_status(dstatus, DMS_ERR_TIMEOUT);
@@ -199,10 +218,6 @@ __device__ __forceinline__ void append(uint32_t* list, unsigned int* count, uint
   list[base + __popc(active & ((1u << lane) - 1u))] = v;
 }
 
-struct Tri {
-  uint64_t* w;
-  uint32_t *na, *nb, *ra, *rb, *res;
-};
 
 // D0: the weight of each critical edge (its lexicographic key).
 __global__ void d0_weights(Dev D, const uint32_t* __restrict__ order,
@@ -216,8 +231,8 @@ __global__ void d0_weights(Dev D, const uint32_t* __restrict__ order,
   uint32_t oa = __ldg(order + a), ob = __ldg(order + b);
   int64_t top = oa > ob ? a : b;
   uint32_t r = local_rank(D, order, top, oa > ob ? ob : oa);
-  T.w[i] = ((uint64_t)(oa > ob ? oa : ob) << 4) | r;
-  T.res[i] = kNone;
+  T.s[i].w = ((uint64_t)(oa > ob ? oa : ob) << 4) | r;
+  T.s[i].res = kNone;
 }
 
 // The two cofacets of critical triangle id (anchor a, type k) in field g
@@ -269,8 +284,8 @@ __global__ void d2_weights(Dev D, const uint32_t* __restrict__ order,
   uint32_t rm, rl;
   local_rank2(D, order, v[it], om, ol, rm, rl);
   uint64_t key = ((uint64_t)o[it] << 8) | (rm << 4) | rl;
-  T.w[i] = kMask44 - key;
-  T.res[i] = kNone;
+  T.s[i].w = kMask44 - key;
+  T.s[i].res = kNone;
 }
 
 // ---------------------------------------------------------------------------
@@ -462,7 +477,8 @@ __global__ void __launch_bounds__(256) walk_each(const W wk, const int64_t* n_de
       if (wk.start(s, j, st, r))
         while (wk.step(st, (uint32_t)(2 * s + j), r, dstatus)) {
         }
-      (j ? T.rb : T.ra)[s] = r;
+      if (j) T.s[s].rb = r;
+      else T.s[s].ra = r;
     }
   }
 }
@@ -473,33 +489,31 @@ __global__ void link_walks(int64_t nt, Tri T, uint32_t* live, unsigned int* live
                         int32_t* dstatus) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= nt) return;
-  const uint32_t n0 = resolve_walk(T.ra, T.rb, T.ra[i], 2 * nt, dstatus);
-  const uint32_t n1 = resolve_walk(T.ra, T.rb, T.rb[i], 2 * nt, dstatus);
+  const uint32_t n0 = resolve_walk(T.s, T.s[i].ra, 2 * nt, dstatus);
+  const uint32_t n1 = resolve_walk(T.s, T.s[i].rb, 2 * nt, dstatus);
   if (n0 == n1) return;
-  T.na[i] = n0;
-  T.nb[i] = n1;
+  T.s[i].na = n0;
+  T.s[i].nb = n1;
   append(live, live_n, (uint32_t)i);
 }
 
 __global__ void init_nodes_d0(const uint32_t* __restrict__ order, const int64_t* __restrict__ crit0,
-                              int64_t nmin, uint32_t* parent, unsigned long long* best,
-                              uint64_t* age) {
+                              int64_t nmin, Nodes nd) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= nmin) return;
-  parent[i] = (uint32_t)i;
-  best[i] = 0ull;
-  age[i] = __ldg(order + crit0[i]);
+  nd.parent[i] = (uint32_t)i;
+  nd.best[i] = 0ull;
+  nd.age[i] = __ldg(order + crit0[i]);
 }
 
 __global__ void init_nodes_d2(Dev D, const uint32_t* __restrict__ order,
-                              const int64_t* __restrict__ crit3, int64_t nmax, uint32_t* parent,
-                              unsigned long long* best, uint64_t* age) {
+                              const int64_t* __restrict__ crit3, int64_t nmax, Nodes nd) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i > nmax) return;
-  parent[i] = (uint32_t)i;
-  best[i] = 0ull;
+  nd.parent[i] = (uint32_t)i;
+  nd.best[i] = 0ull;
   if (i == 0) {
-    age[0] = 0;  // OUTSIDE is older than every maximum
+    nd.age[0] = 0;  // OUTSIDE is older than every maximum
     return;
   }
   int64_t id = crit3[i - 1];
@@ -522,34 +536,34 @@ __global__ void init_nodes_d2(Dev D, const uint32_t* __restrict__ order,
   uint32_t h = max(r[0], max(r[1], r[2])), l = min(r[0], min(r[1], r[2]));
   uint32_t m = r[0] + r[1] + r[2] - h - l;
   uint64_t key = ((uint64_t)o[it] << 12) | (h << 8) | (m << 4) | l;
-  age[i] = (kMask44 - key) + 1;  // a higher maximum is older
+  nd.age[i] = (kMask44 - key) + 1;  // a higher maximum is older
 }
 
-__device__ __forceinline__ uint32_t find_root(uint32_t* parent, uint32_t x) {
-  uint32_t p = parent[x];
+__device__ __forceinline__ uint32_t find_root(Nodes nd, uint32_t x) {
+  uint32_t p = nd.parent[x];
   while (p != x) {
-    uint32_t gp = parent[p];
-    if (gp != p) parent[x] = gp;  // path halving: only ever points further up
+    uint32_t gp = nd.parent[p];
+    if (gp != p) nd.parent[x] = gp;  // path halving: only ever points further up
     x = gp;
-    p = parent[x];
+    p = nd.parent[x];
   }
   return x;
 }
 
 __global__ void round_find(const uint32_t* __restrict__ live, const unsigned int* __restrict__ live_n,
-                           Tri T, uint32_t* parent, unsigned long long* best, uint64_t round) {
+                           Tri T, Nodes nd, uint64_t round) {
   unsigned int n = *live_n;
   for (unsigned int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     uint32_t i = live[j];
     // roots only ever gain parents: search from last round's roots
-    uint32_t a = find_root(parent, round == 1 ? T.na[i] : T.ra[i]);
-    uint32_t b = find_root(parent, round == 1 ? T.nb[i] : T.rb[i]);
-    T.ra[i] = a;
-    T.rb[i] = b;
+    uint32_t a = find_root(nd, round == 1 ? T.s[i].na : T.s[i].ra);
+    uint32_t b = find_root(nd, round == 1 ? T.s[i].nb : T.s[i].rb);
+    T.s[i].ra = a;
+    T.s[i].rb = b;
     if (a == b) continue;
-    unsigned long long tv = (round << 44) | (kMask44 - T.w[i]);
-    atomicMax(best + a, tv);
-    atomicMax(best + b, tv);
+    unsigned long long tv = (round << 44) | (kMask44 - T.s[i].w);
+    atomicMax(nd.best + a, tv);
+    atomicMax(nd.best + b, tv);
   }
 }
 
@@ -564,17 +578,16 @@ __global__ void round_find(const uint32_t* __restrict__ live, const unsigned int
 // A root dies through its own lightest saddle only, so it dies at most once
 // per round, and the links never form a cycle (each points to an older root).
 __global__ void round_merge(const uint32_t* __restrict__ live, const unsigned int* __restrict__ live_n,
-                            Tri T, uint32_t* parent, const unsigned long long* __restrict__ best,
-                            const uint64_t* __restrict__ age, uint64_t round, uint32_t* next,
+                            Tri T, Nodes nd, uint64_t round, uint32_t* next,
                             unsigned int* next_n) {
   unsigned int n = *live_n;
   for (unsigned int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
     uint32_t i = live[j];
-    uint32_t a = T.ra[i], b = T.rb[i];
+    uint32_t a = T.s[i].ra, b = T.s[i].rb;
     if (a == b) continue;  // both ends already joined: no pair (Alg. 1, r0 == r1)
-    unsigned long long tv = (round << 44) | (kMask44 - T.w[i]);
-    const bool la = best[a] == tv, lb = best[b] == tv;
-    const uint64_t ga = age[a], gb = age[b];
+    unsigned long long tv = (round << 44) | (kMask44 - T.s[i].w);
+    const bool la = nd.best[a] == tv, lb = nd.best[b] == tv;
+    const uint64_t ga = nd.age[a], gb = nd.age[b];
     uint32_t young = kNone, old = kNone;
     if (la && lb) {
       young = ga > gb ? a : b;
@@ -587,8 +600,8 @@ __global__ void round_merge(const uint32_t* __restrict__ live, const unsigned in
       old = a;
     }
     if (young != kNone) {
-      parent[young] = old;
-      T.res[i] = young;
+      nd.parent[young] = old;
+      T.s[i].res = young;
     } else {
       append(next, next_n, i);
     }
@@ -602,25 +615,25 @@ __global__ void gather_live(const uint32_t* __restrict__ live, const unsigned in
                             const Tri T, unsigned long long* keys, uint32_t* vals) {
   unsigned int n = *live_n;
   for (unsigned int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-    keys[j] = T.w[live[j]];
+    keys[j] = T.s[live[j]].w;
     vals[j] = live[j];
   }
 }
 
 __global__ void sequential_finish(const uint32_t* __restrict__ sorted, const unsigned int* __restrict__ live_n,
-                                  Tri T, uint32_t* parent, const uint64_t* __restrict__ age) {
+                                  Tri T, Nodes nd) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   unsigned int n = *live_n;
   for (unsigned int j = 0; j < n; ++j) {
     uint32_t i = sorted[j];
-    uint32_t a = T.na[i], b = T.nb[i];
-    while (parent[a] != a) a = parent[a] = parent[parent[a]];
-    while (parent[b] != b) b = parent[b] = parent[parent[b]];
+    uint32_t a = T.s[i].na, b = T.s[i].nb;
+    while (nd.parent[a] != a) a = nd.parent[a] = nd.parent[nd.parent[a]];
+    while (nd.parent[b] != b) b = nd.parent[b] = nd.parent[nd.parent[b]];
     if (a == b) continue;
-    uint32_t young = age[a] > age[b] ? a : b;
+    uint32_t young = nd.age[a] > nd.age[b] ? a : b;
     uint32_t old = young == a ? b : a;
-    parent[young] = old;
-    T.res[i] = young;
+    nd.parent[young] = old;
+    T.s[i].res = young;
   }
 }
 
@@ -633,7 +646,7 @@ __global__ void __launch_bounds__(PNT) count_pairs(const Tri T, int64_t nsad, lo
   int c = 0;
   for (int k = 0; k < PITEMS; ++k) {
     int64_t i = base + k;
-    if (i < nsad && T.res[i] != kNone) ++c;
+    if (i < nsad && T.s[i].res != kNone) ++c;
   }
   long long t;
   scan64::block_excl(c, tmp, &t);
@@ -657,7 +670,7 @@ __device__ __forceinline__ int64_t top_of(const Dev& D, const uint32_t* order, c
 __device__ __forceinline__ void write_one_d0(const Dev& D, const float* f, const uint32_t* order,
                                             const int64_t* crit0, const int64_t* crit1,
                                             const Tri& T, int64_t i, dms_pair* out) {
-  int64_t m = crit0[T.res[i]];
+  int64_t m = crit0[T.s[i].res];
   int64_t id = crit1[i];
   int64_t a = id / 7;
   int k = (int)(id - a * 7);
@@ -676,7 +689,7 @@ __device__ __forceinline__ void write_one_d0(const Dev& D, const float* f, const
 __device__ __forceinline__ void write_one_d2(const Dev& D, const float* f, const uint32_t* order,
                                             const int64_t* crit2, const int64_t* crit3,
                                             const Tri& T, int64_t i, dms_pair* out) {
-  int64_t tet = crit3[T.res[i] - 1];  // node 0 (OUTSIDE) never dies
+  int64_t tet = crit3[T.s[i].res - 1];  // node 0 (OUTSIDE) never dies
   int64_t tri = crit2[i];
   int64_t a = tri / 12;
   int k = (int)(tri - a * 12);
@@ -714,12 +727,12 @@ __global__ void __launch_bounds__(PNT) write_pairs(int dim, Dev D, const float* 
   int c = 0;
   for (int k = 0; k < PITEMS; ++k) {
     int64_t i = base + k;
-    if (i < nsad && T.res[i] != kNone) ++c;
+    if (i < nsad && T.s[i].res != kNone) ++c;
   }
   long long pos = scan64::block_excl(c, tmp, nullptr) + toff[blockIdx.x];
   for (int k = 0; k < PITEMS; ++k) {
     int64_t i = base + k;
-    if (i >= nsad || T.res[i] == kNone) continue;
+    if (i >= nsad || T.s[i].res == kNone) continue;
     if (pos < cap) {
       if (dim == 0) write_one_d0(D, f, order, critA, critB, T, i, out + pos);
       else write_one_d2(D, f, order, critA, critB, T, i, out + pos);
@@ -748,9 +761,7 @@ struct DiagWs {
   Tri T0, T2;
   uint32_t *live0, *live1;
   unsigned int* ctr;  // [0..1] live counts, [2] pair count
-  uint32_t* parent;
-  unsigned long long* best;
-  uint64_t* age;
+  Nodes nd;  // union-find nodes: parent, best live saddle, age
   uint32_t* dir;  // kDirBuckets + 1 bucket starts
   uint32_t* claim;  // one word per tet id: the dual walk that passed it
   int64_t nclaim;
@@ -763,22 +774,15 @@ DiagWs carve_diag(void* base, const int64_t* nc, int64_t nvert) {
   DiagWs w;
   const int64_t nsad = std::max<int64_t>(std::max<int64_t>(nc[1], nc[2]), 1);
   const int64_t nnode = std::max<int64_t>(nc[0], nc[3] + 1);
-  auto tri = [&](Tri& t) {
-    t.w = c.take<uint64_t>(nsad);
-    t.na = c.take<uint32_t>(nsad);
-    t.nb = c.take<uint32_t>(nsad);
-    t.ra = c.take<uint32_t>(nsad);
-    t.rb = c.take<uint32_t>(nsad);
-    t.res = c.take<uint32_t>(nsad);
-  };
-  tri(w.T0);
+  static_assert(sizeof(Sad) == 32, "one sector per saddle");
+  w.T0.s = c.take<Sad>(nsad);
   w.T2 = w.T0;  // D0 and D2 run one after the other and share the arrays
   w.live0 = c.take<uint32_t>(nsad);
   w.live1 = c.take<uint32_t>(nsad);
   w.ctr = c.take<unsigned int>(8);
-  w.parent = c.take<uint32_t>(nnode);
-  w.best = c.take<unsigned long long>(nnode);
-  w.age = c.take<uint64_t>(nnode);
+  w.nd.parent = c.take<uint32_t>(nnode);
+  w.nd.best = c.take<unsigned long long>(nnode);
+  w.nd.age = c.take<uint64_t>(nnode);
   w.dir = c.take<uint32_t>(kDirBuckets + 1);
   w.nclaim = 6 * nvert;
   w.claim = c.take<uint32_t>(w.nclaim);
@@ -805,14 +809,14 @@ int run_rounds(DiagWs& w, Tri T, cudaStream_t s, int32_t* dstatus) {
       unsigned int blocks = (h + 255) / 256;
       gather_live<<<blocks, 256, 0, s>>>(cur, cur_n, T, w.rb.ka, w.rb.va); count_launch();
       bool in_a = radix64::sort(w.rb, h, 44, s);
-      sequential_finish<<<1, 32, 0, s>>>(in_a ? w.rb.va : w.rb.vb, cur_n, T, w.parent, w.age); count_launch();
+      sequential_finish<<<1, 32, 0, s>>>(in_a ? w.rb.va : w.rb.vb, cur_n, T, w.nd); count_launch();
       break;
     }
     prev = h;
     unsigned int blocks = (unsigned int)std::min<int64_t>((h + 255) / 256, 1 << 16);
     DMS_CUDA_OK(cudaMemsetAsync(nxt_n, 0, sizeof(unsigned int), s));
-    round_find<<<blocks, 256, 0, s>>>(cur, cur_n, T, w.parent, w.best, round); count_launch();
-    round_merge<<<blocks, 256, 0, s>>>(cur, cur_n, T, w.parent, w.best, w.age, round, nxt, nxt_n); count_launch();
+    round_find<<<blocks, 256, 0, s>>>(cur, cur_n, T, w.nd, round); count_launch();
+    round_merge<<<blocks, 256, 0, s>>>(cur, cur_n, T, w.nd, round, nxt, nxt_n); count_launch();
     std::swap(cur, nxt);
     std::swap(cur_n, nxt_n);
   }
@@ -863,7 +867,7 @@ int launch_diagram(const float* f, const uint32_t* order, const uint8_t* desc, c
   // ---- D0
   DMS_CUDA_OK(cudaMemsetAsync(w.ctr, 0, 8 * sizeof(unsigned int), s));
   if (nc[0] > 0) {
-    init_nodes_d0<<<nb(nc[0]), TB, 0, s>>>(order, crit0, nc[0], w.parent, w.best, w.age); count_launch();
+    init_nodes_d0<<<nb(nc[0]), TB, 0, s>>>(order, crit0, nc[0], w.nd); count_launch();
     write_essential<<<nb(nc[0]), TB, 0, s>>>(f, order, crit0, nc[0], ess); count_launch();
   }
   if (nc[1] > 0) {
@@ -882,7 +886,7 @@ int launch_diagram(const float* f, const uint32_t* order, const uint8_t* desc, c
 
   // ---- D2
   DMS_CUDA_OK(cudaMemsetAsync(w.ctr, 0, 8 * sizeof(unsigned int), s));
-  init_nodes_d2<<<nb(nc[3] + 1), TB, 0, s>>>(D, order, crit3, nc[3], w.parent, w.best, w.age); count_launch();
+  init_nodes_d2<<<nb(nc[3] + 1), TB, 0, s>>>(D, order, crit3, nc[3], w.nd); count_launch();
   if (nc[2] > 0) {
     Dir d3dir{crit3, nc[3], w.dir, dir_shift(6 * g.n)};
     build_dir<<<nb(kDirBuckets + 1), TB, 0, s>>>(crit3, nc[3], d3dir.shift, w.dir); count_launch();
@@ -978,14 +982,13 @@ __global__ void b_build_dir(const int64_t* __restrict__ list, const int64_t* __r
 }
 
 __global__ void b_init_nodes_d0(const uint32_t* __restrict__ order, const int64_t* __restrict__ crit0,
-                                const int64_t* __restrict__ cnt, uint32_t* parent,
-                                unsigned long long* best, uint64_t* age) {
+                                const int64_t* __restrict__ cnt, Nodes nd) {
   const int64_t n = cnt[0];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    parent[i] = (uint32_t)i;
-    best[i] = 0ull;
-    age[i] = __ldg(order + crit0[i]);
+    nd.parent[i] = (uint32_t)i;
+    nd.best[i] = 0ull;
+    nd.age[i] = __ldg(order + crit0[i]);
   }
 }
 
@@ -1025,21 +1028,21 @@ __global__ void b_d0_weights(const FieldTab ft, const uint32_t* __restrict__ ord
     const uint32_t oa = __ldg(order + a), ob = __ldg(order + b);
     const int64_t top = oa > ob ? a : b;
     const uint32_t r = local_rank_f(g, fd.offset, order, top, oa > ob ? ob : oa);
-    T.w[i] = ((uint64_t)(oa > ob ? oa : ob) << 4) | r;
-    T.res[i] = kNone;
+    T.s[i].w = ((uint64_t)(oa > ob ? oa : ob) << 4) | r;
+    T.s[i].res = kNone;
   }
 }
 
 __global__ void b_init_nodes_d2(const FieldTab ft, const uint32_t* __restrict__ order,
                                 const int64_t* __restrict__ crit3, const int64_t* __restrict__ cnt,
-                                uint32_t* parent, unsigned long long* best, uint64_t* age) {
+                                Nodes nd) {
   const int64_t nmax = cnt[3];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= nmax;
        i += (int64_t)gridDim.x * blockDim.x) {
-    parent[i] = (uint32_t)i;
-    best[i] = 0ull;
+    nd.parent[i] = (uint32_t)i;
+    nd.best[i] = 0ull;
     if (i == 0) {
-      age[0] = 0;  // OUTSIDE is older than every maximum of every field
+      nd.age[0] = 0;  // OUTSIDE is older than every maximum of every field
       continue;
     }
     const int64_t id = crit3[i - 1];
@@ -1063,7 +1066,7 @@ __global__ void b_init_nodes_d2(const FieldTab ft, const uint32_t* __restrict__ 
     const uint32_t h = max(r[0], max(r[1], r[2])), l = min(r[0], min(r[1], r[2]));
     const uint32_t m = r[0] + r[1] + r[2] - h - l;
     const uint64_t key = ((uint64_t)o[it] << 12) | (h << 8) | (m << 4) | l;
-    age[i] = (kMask44 - key) + 1;
+    nd.age[i] = (kMask44 - key) + 1;
   }
 }
 
@@ -1093,8 +1096,8 @@ __global__ void b_d2_weights(const FieldTab ft, const uint32_t* __restrict__ ord
     const uint32_t rm = local_rank_f(g, fd.offset, order, v[it], om);
     const uint32_t rl = local_rank_f(g, fd.offset, order, v[it], ol);
     const uint64_t key = ((uint64_t)o[it] << 8) | (rm << 4) | rl;
-    T.w[i] = kMask44 - key;
-    T.res[i] = kNone;
+    T.s[i].w = kMask44 - key;
+    T.s[i].res = kNone;
   }
 }
 
@@ -1103,11 +1106,11 @@ __global__ void b_link_walks(const int64_t* __restrict__ n_dev, Tri T, uint32_t*
   const int64_t nt = *n_dev;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nt;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t n0 = resolve_walk(T.ra, T.rb, T.ra[i], 2 * nt, dstatus);
-    const uint32_t n1 = resolve_walk(T.ra, T.rb, T.rb[i], 2 * nt, dstatus);
+    const uint32_t n0 = resolve_walk(T.s, T.s[i].ra, 2 * nt, dstatus);
+    const uint32_t n1 = resolve_walk(T.s, T.s[i].rb, 2 * nt, dstatus);
     if (n0 == n1) continue;
-    T.na[i] = n0;
-    T.nb[i] = n1;
+    T.s[i].na = n0;
+    T.s[i].nb = n1;
     append(live, live_n, (uint32_t)i);
   }
 }
@@ -1117,7 +1120,7 @@ __global__ void b_link_walks(const int64_t* __restrict__ n_dev, Tri T, uint32_t*
 constexpr int kFinishMax = 4096;
 __global__ void __launch_bounds__(1024) b_finish(const uint32_t* __restrict__ live,
                                                  const unsigned int* __restrict__ live_n, Tri T,
-                                                 uint32_t* parent, const uint64_t* __restrict__ age,
+                                                 Nodes nd,
                                                  int32_t* dstatus) {
   __shared__ unsigned long long key[kFinishMax];
   __shared__ uint32_t idx[kFinishMax];
@@ -1128,7 +1131,7 @@ __global__ void __launch_bounds__(1024) b_finish(const uint32_t* __restrict__ li
     return;
   }
   for (int i = threadIdx.x; i < kFinishMax; i += blockDim.x) {
-    key[i] = i < (int)n ? T.w[live[i]] : ~0ull;
+    key[i] = i < (int)n ? T.s[live[i]].w : ~0ull;
     idx[i] = i < (int)n ? live[i] : kNone;
   }
   __syncthreads();
@@ -1153,13 +1156,13 @@ __global__ void __launch_bounds__(1024) b_finish(const uint32_t* __restrict__ li
   if (threadIdx.x != 0) return;
   for (unsigned int j = 0; j < n; ++j) {
     const uint32_t i = idx[j];
-    uint32_t a = T.na[i], b = T.nb[i];
-    while (parent[a] != a) a = parent[a] = parent[parent[a]];
-    while (parent[b] != b) b = parent[b] = parent[parent[b]];
+    uint32_t a = T.s[i].na, b = T.s[i].nb;
+    while (nd.parent[a] != a) a = nd.parent[a] = nd.parent[nd.parent[a]];
+    while (nd.parent[b] != b) b = nd.parent[b] = nd.parent[nd.parent[b]];
     if (a == b) continue;
-    const uint32_t young = age[a] > age[b] ? a : b;
-    parent[young] = young == a ? b : a;
-    T.res[i] = young;
+    const uint32_t young = nd.age[a] > nd.age[b] ? a : b;
+    nd.parent[young] = young == a ? b : a;
+    T.s[i].res = young;
   }
 }
 
@@ -1170,7 +1173,7 @@ __global__ void b_count_fields(const FieldTab ft, const Tri T, const int64_t* __
   const int64_t n = *n_dev;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    if (T.res[i] != kNone) atomicAdd(fcount + field_of_vertex(ft, crit[i] / per_anchor), 1ull);
+    if (T.s[i].res != kNone) atomicAdd(fcount + field_of_vertex(ft, crit[i] / per_anchor), 1ull);
 }
 
 __global__ void b_field_offsets(const unsigned long long* __restrict__ fcount, int nfields,
@@ -1195,7 +1198,7 @@ __global__ void __launch_bounds__(PNT) b_count_pairs(const Tri T, const int64_t*
   int c = 0;
   for (int k = 0; k < PITEMS; ++k) {
     const int64_t i = base + k;
-    if (i < nsad && T.res[i] != kNone) ++c;
+    if (i < nsad && T.s[i].res != kNone) ++c;
   }
   long long t;
   scan64::block_excl(c, tmp, &t);
@@ -1216,16 +1219,16 @@ __global__ void __launch_bounds__(PNT) b_write_pairs(int dim, const FieldTab ft,
   int c = 0;
   for (int k = 0; k < PITEMS; ++k) {
     const int64_t i = base + k;
-    if (i < nsad && T.res[i] != kNone) ++c;
+    if (i < nsad && T.s[i].res != kNone) ++c;
   }
   long long pos = scan64::block_excl(c, tmp, nullptr) + toff[blockIdx.x];
   for (int k = 0; k < PITEMS; ++k) {
     const int64_t i = base + k;
-    if (i >= nsad || T.res[i] == kNone) continue;
+    if (i >= nsad || T.s[i].res == kNone) continue;
     if (pos < cap) {
       dms_pair p;
       if (dim == 0) {
-        const int64_t m = critA[T.res[i]];
+        const int64_t m = critA[T.s[i].res];
         const int64_t id = critB[i];
         const int64_t a = id / 7;
         const int kk = (int)(id - a * 7);
@@ -1240,7 +1243,7 @@ __global__ void __launch_bounds__(PNT) b_write_pairs(int dim, const FieldTab ft,
         p.birth_vtx = (uint32_t)(m - fd.offset);
         p.death_vtx = (uint32_t)(top - fd.offset);
       } else {
-        const int64_t tet = critB[T.res[i] - 1];
+        const int64_t tet = critB[T.s[i].res - 1];
         const int64_t tri = critA[i];
         const int64_t a = tri / 12;
         const int kk = (int)(tri - a * 12);
@@ -1314,12 +1317,12 @@ int launch_diagram_batch(const float* f, const uint32_t* order, const uint8_t* d
     unsigned int* nxt_n = w.ctr + 1;
     for (int r = 1; r <= kBatchRounds; ++r) {
       mem_ok = mem_ok && cudaMemsetAsync(nxt_n, 0, sizeof(unsigned int), s) == cudaSuccess;
-      round_find<<<G, TB, 0, s>>>(cur, cur_n, T, w.parent, w.best, (uint64_t)r); count_launch();
-      round_merge<<<G, TB, 0, s>>>(cur, cur_n, T, w.parent, w.best, w.age, (uint64_t)r, nxt, nxt_n); count_launch();
+      round_find<<<G, TB, 0, s>>>(cur, cur_n, T, w.nd, (uint64_t)r); count_launch();
+      round_merge<<<G, TB, 0, s>>>(cur, cur_n, T, w.nd, (uint64_t)r, nxt, nxt_n); count_launch();
       std::swap(cur, nxt);
       std::swap(cur_n, nxt_n);
     }
-    b_finish<<<1, 1024, 0, s>>>(cur, cur_n, T, w.parent, w.age, dstatus); count_launch();
+    b_finish<<<1, 1024, 0, s>>>(cur, cur_n, T, w.nd, dstatus); count_launch();
   };
   auto write = [&](int dim, Tri T, const int64_t* critA, const int64_t* critB, const int64_t* n_dev,
                    dms_pair* out, int64_t* offs, int64_t* total, unsigned long long* fc) {
@@ -1333,7 +1336,7 @@ int launch_diagram_batch(const float* f, const uint32_t* order, const uint8_t* d
 
   // ---- D0
   DMS_CUDA_OK(cudaMemsetAsync(w.ctr, 0, 8 * sizeof(unsigned int), s));
-  b_init_nodes_d0<<<G, TB, 0, s>>>(order, crit[0], cnt_dev, w.parent, w.best, w.age); count_launch();
+  b_init_nodes_d0<<<G, TB, 0, s>>>(order, crit[0], cnt_dev, w.nd); count_launch();
   b_essential<<<G, TB, 0, s>>>(ft, f, order, crit[0], cnt_dev, ess); count_launch();
   b_build_dir<<<dir_blocks, TB, 0, s>>>(crit[0], cnt_dev + 0, shift0, w.dir); count_launch();
   const Dir dir0{crit[0], caps[0], w.dir, shift0};
@@ -1349,7 +1352,7 @@ int launch_diagram_batch(const float* f, const uint32_t* order, const uint8_t* d
 
   // ---- D2
   DMS_CUDA_OK(cudaMemsetAsync(w.ctr, 0, 8 * sizeof(unsigned int), s));
-  b_init_nodes_d2<<<G, TB, 0, s>>>(ft, order, crit[3], cnt_dev, w.parent, w.best, w.age); count_launch();
+  b_init_nodes_d2<<<G, TB, 0, s>>>(ft, order, crit[3], cnt_dev, w.nd); count_launch();
   b_build_dir<<<dir_blocks, TB, 0, s>>>(crit[3], cnt_dev + 3, shift3, w.dir); count_launch();
   const Dir dir3{crit[3], caps[3], w.dir, shift3};
   DMS_CUDA_OK(cudaMemsetAsync(w.claim, 0xFF, w.nclaim * sizeof(uint32_t), s));

@@ -387,3 +387,68 @@ def test_local_elder_rule_limit(rng):
     r = oracle.run(f, gradient=True, diagrams=False)
     outcomes = {oracle.d0_edge_local(f, int(e), limit=3)[0] for e in r.crit(1)}
     assert -1 in outcomes
+
+
+def _bottleneck(a, b):
+    """Bottleneck distance between two finite diagrams (arrays [n, 2]) under
+    the L-infinity norm, points free to match the diagonal: the smallest
+    candidate threshold at which the usual bipartite graph (points of a and
+    diagonal copies of b's points against points of b and diagonal copies of
+    a's) has a perfect matching."""
+    nx_ = pytest.importorskip("networkx")
+    a = np.asarray(a, dtype=np.float64).reshape(-1, 2)
+    b = np.asarray(b, dtype=np.float64).reshape(-1, 2)
+    da, db = (a[:, 1] - a[:, 0]) / 2, (b[:, 1] - b[:, 0]) / 2
+    cand = {0.0, *da.tolist(), *db.tolist()}
+    for p in a:
+        for q in b:
+            cand.add(float(np.max(np.abs(p - q))))
+    for t in sorted(cand):
+        g = nx_.Graph()
+        left = [("a", i) for i in range(len(a))] + [("da", j) for j in range(len(b))]
+        right = [("b", j) for j in range(len(b))] + [("db", i) for i in range(len(a))]
+        g.add_nodes_from(left, bipartite=0)
+        g.add_nodes_from(right, bipartite=1)
+        for i in range(len(a)):
+            for j in range(len(b)):
+                if np.max(np.abs(a[i] - b[j])) <= t:
+                    g.add_edge(("a", i), ("b", j))
+            if da[i] <= t:
+                g.add_edge(("a", i), ("db", i))
+        for j in range(len(b)):
+            if db[j] <= t:
+                g.add_edge(("da", j), ("b", j))
+        for j in range(len(b)):
+            for i in range(len(a)):
+                g.add_edge(("da", j), ("db", i))
+        m = nx_.bipartite.hopcroft_karp_matching(g, top_nodes=left)
+        if len(m) // 2 == len(left):
+            return t
+    return float("inf")
+
+
+def test_bottleneck_helper_on_hand_diagrams():
+    assert _bottleneck([[0, 1]], [[0, 1]]) == 0
+    assert _bottleneck([[0, 1]], [[0.1, 1.2]]) == pytest.approx(0.2)
+    assert _bottleneck([[0, 1]], []) == pytest.approx(0.5)  # to the diagonal
+    assert _bottleneck([[0, 4], [1, 1.2]], [[0.5, 4]]) == pytest.approx(0.5)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_diagrams_are_stable_under_perturbation(seed):
+    """Stability of persistence diagrams: the bottleneck distance between the
+    D0 (and D2) value diagrams of f and f + e is at most max |e|, and the
+    essential minimum moves by at most max |e| too."""
+    rng = np.random.default_rng(100 + seed)
+    f = rng.random((5, 6, 7)).astype(np.float32)
+    e = ((rng.random(f.shape) - 0.5) * 0.02).astype(np.float32)
+    g = (f + e).astype(np.float32)
+    eps = float(np.max(np.abs(g.astype(np.float64) - f.astype(np.float64))))
+    rf, rg = oracle.run(f), oracle.run(g)
+    for which in (oracle.D0, oracle.D2):
+        pf, pg = rf.get(which), rg.get(which)
+        a = np.stack([pf["birth"], pf["death"]], 1)
+        b = np.stack([pg["birth"], pg["death"]], 1)
+        assert _bottleneck(a, b) <= eps + 1e-9
+    ef, eg = rf.get(oracle.D0_ESSENTIAL), rg.get(oracle.D0_ESSENTIAL)
+    assert abs(float(ef["birth"][0]) - float(eg["birth"][0])) <= eps + 1e-9

@@ -27,9 +27,15 @@ __device__ __forceinline__ void anchor_counts(uint8_t d, uint64_t r, int c[4]) {
   c[3] = __popcll(r & (r >> 1) & (r >> 2) & kTetLsb);
 }
 
+// A thread works on CITEMS consecutive anchors, so consecutive threads read
+// shared memory CITEMS elements apart; one pad element per CITEMS spreads
+// those reads over the banks.
+constexpr int CPAD = CTILE + CTILE / CITEMS;
+__device__ __forceinline__ int padded(int i) { return i + i / CITEMS; }
+
 struct TileSmem {
-  unsigned long long rec[CTILE];
-  uint8_t desc[CTILE];
+  unsigned long long rec[CPAD];
+  uint8_t desc[CPAD];
   long long tmp[32];
 };
 
@@ -37,8 +43,8 @@ __device__ __forceinline__ void stage(TileSmem& sm, const uint8_t* desc, const u
                                       int64_t a0, int64_t n) {
   for (int i = threadIdx.x; i < CTILE; i += CNT) {
     int64_t a = a0 + i;
-    sm.rec[i] = a < n ? __ldg(reinterpret_cast<const unsigned long long*>(rec) + a) : 0ull;
-    sm.desc[i] = a < n ? __ldg(desc + a) : (uint8_t)0;
+    sm.rec[padded(i)] = a < n ? __ldg(reinterpret_cast<const unsigned long long*>(rec) + a) : 0ull;
+    sm.desc[padded(i)] = a < n ? __ldg(desc + a) : (uint8_t)0;
   }
   __syncthreads();
 }
@@ -53,7 +59,7 @@ __global__ void __launch_bounds__(CNT) count_kernel(const uint8_t* __restrict__ 
   for (int k = 0; k < CITEMS; ++k) {
     int i = threadIdx.x * CITEMS + k;
     int c[4];
-    anchor_counts(sm.desc[i], sm.rec[i], c);
+    anchor_counts(sm.desc[padded(i)], sm.rec[padded(i)], c);
     if (a0 + i >= n) c[0] = 0;
     for (int d = 0; d < 4; ++d) tot[d] += c[d];
   }
@@ -78,7 +84,7 @@ __global__ void __launch_bounds__(CNT) write_kernel(const uint8_t* __restrict__ 
   for (int k = 0; k < CITEMS; ++k) {
     int i = threadIdx.x * CITEMS + k;
     int c[4];
-    anchor_counts(sm.desc[i], sm.rec[i], c);
+    anchor_counts(sm.desc[padded(i)], sm.rec[padded(i)], c);
     if (a0 + i >= n) c[0] = 0;
     for (int d = 0; d < 4; ++d) tot[d] += c[d];
   }
@@ -91,8 +97,8 @@ __global__ void __launch_bounds__(CNT) write_kernel(const uint8_t* __restrict__ 
     int i = threadIdx.x * CITEMS + k;
     int64_t a = a0 + i;
     if (a >= n) break;
-    uint64_t r = sm.rec[i];
-    if (sm.desc[i] == 15) {
+    uint64_t r = sm.rec[padded(i)];
+    if (sm.desc[padded(i)] == 15) {
       if (off[0] < cap0) c0[off[0]] = a;
       ++off[0];
     }

@@ -56,6 +56,11 @@ struct Nodes {
   uint32_t* parent;
   unsigned long long* best;
   uint64_t* age;
+  // a node that never dies (OUTSIDE in D2, kNone in D0): it takes no tags --
+  // a saddle to it merges by the downhill rule exactly when the mutual rule
+  // would, and thousands of boundary saddles would otherwise contend for
+  // its tag
+  uint32_t immortal;
 };
 
 // one saddle of the pairing, in one 32-byte sector: its weight, its two
@@ -301,6 +306,10 @@ struct OneField {
     out = g;
     off = 0;
   }
+  __device__ __forceinline__ void coords(const Grid&, int64_t v, int64_t& x, int64_t& y,
+                                         int64_t& z) const {
+    xyz(g, v, x, y, z);
+  }
 };
 
 // a batch: the field that holds an anchor, by binary search of the table
@@ -321,6 +330,10 @@ struct ManyFields {
     out.sxy = (int64_t)d.nx * d.ny;
     out.n = out.sxy * d.nz;
     off = d.offset;
+  }
+  __device__ __forceinline__ void coords(const Grid& g, int64_t v, int64_t& x, int64_t& y,
+                                         int64_t& z) const {
+    xyz(g, v, x, y, z);
   }
 };
 
@@ -355,18 +368,21 @@ struct DescWalk {
     return true;
   }
   // one step; false when the walk has ended with result r
+  // the gradient load and the claim of the current vertex are independent,
+  // so both are in flight together (a minimum may be claimed too: a walk
+  // that meets it there takes the claiming walk's end, the same minimum)
   __device__ __forceinline__ bool step(State& st, uint32_t w, uint32_t& r,
                                        int32_t* dstatus) const {
     const uint8_t d = __ldg(desc + st.v);
+    const uint32_t old = atomicCAS(claim + st.v, kUnclaimed, w);
+    if (old != kUnclaimed) {
+      r = kLinkBit | old;
+      return false;
+    }
     if (d >= 14) {
       const int64_t pos = dir_find_fwd(dir0.list, dir0.start, dir0.shift, st.v);
       if (pos < 0) set_status(dstatus, DMS_ERR_ARG);
       r = pos < 0 ? 0u : (uint32_t)pos;
-      return false;
-    }
-    const uint32_t old = atomicCAS(claim + st.v, kUnclaimed, w);
-    if (old != kUnclaimed) {
-      r = kLinkBit | old;
       return false;
     }
     st.v += slot_delta_g(st.g, d);
@@ -400,7 +416,7 @@ struct DualWalk {
     int64_t off;
     fields.get(a, st.g, off);
     int64_t ax, ay, az;
-    xyz(st.g, a - off, ax, ay, az);
+    fields.coords(st.g, a - off, ax, ay, az);
     int64_t cof[2];
     tri_cofacets(st.g, a, k, ax, ay, az, cof);
     const int64_t t = cof[j];
@@ -410,13 +426,22 @@ struct DualWalk {
     }
     st.b = t / 6;
     st.k = (int)(t - st.b * 6);
-    xyz(st.g, st.b - off, st.bx, st.by, st.bz);
+    fields.coords(st.g, st.b - off, st.bx, st.by, st.bz);
     st.it = 0;
     return true;
   }
+  // record load and claim in flight together, as for the descending walks
+  // (a critical tet may be claimed: the walks that meet it there take the
+  // claiming walk's end, that tet)
   __device__ __forceinline__ bool step(State& st, uint32_t w, uint32_t& r,
                                        int32_t* dstatus) const {
-    const uint32_t code = (uint32_t)(__ldg(rec + st.b) >> (33 + 3 * st.k)) & 7u;
+    const uint64_t rw = __ldg(rec + st.b);
+    const uint32_t old = atomicCAS(claim + st.b * 6 + st.k, kUnclaimed, w);
+    if (old != kUnclaimed) {
+      r = kLinkBit | old;
+      return false;
+    }
+    const uint32_t code = (uint32_t)(rw >> (33 + 3 * st.k)) & 7u;
     if (code == 7u) {
       const int64_t pos = dir_find_fwd(dir3.list, dir3.start, dir3.shift, st.b * 6 + st.k);
       if (pos < 0) set_status(dstatus, DMS_ERR_ARG);
@@ -426,11 +451,6 @@ struct DualWalk {
     if (code < 1u || code > 4u) {
       set_status(dstatus, DMS_ERR_ARG);
       r = 0;
-      return false;
-    }
-    const uint32_t old = atomicCAS(claim + st.b * 6 + st.k, kUnclaimed, w);
-    if (old != kUnclaimed) {
-      r = kLinkBit | old;
       return false;
     }
     const int c1 = cTetC[st.k][0], c2 = cTetC[st.k][1];
@@ -562,8 +582,8 @@ __global__ void round_find(const uint32_t* __restrict__ live, const unsigned int
     T.s[i].rb = b;
     if (a == b) continue;
     unsigned long long tv = (round << 44) | (kMask44 - T.s[i].w);
-    atomicMax(nd.best + a, tv);
-    atomicMax(nd.best + b, tv);
+    if (a != nd.immortal) atomicMax(nd.best + a, tv);
+    if (b != nd.immortal) atomicMax(nd.best + b, tv);
   }
 }
 
@@ -586,7 +606,8 @@ __global__ void round_merge(const uint32_t* __restrict__ live, const unsigned in
     uint32_t a = T.s[i].ra, b = T.s[i].rb;
     if (a == b) continue;  // both ends already joined: no pair (Alg. 1, r0 == r1)
     unsigned long long tv = (round << 44) | (kMask44 - T.s[i].w);
-    const bool la = nd.best[a] == tv, lb = nd.best[b] == tv;
+    const bool la = a != nd.immortal && nd.best[a] == tv;
+    const bool lb = b != nd.immortal && nd.best[b] == tv;
     const uint64_t ga = nd.age[a], gb = nd.age[b];
     uint32_t young = kNone, old = kNone;
     if (la && lb) {
@@ -783,6 +804,7 @@ DiagWs carve_diag(void* base, const int64_t* nc, int64_t nvert) {
   w.nd.parent = c.take<uint32_t>(nnode);
   w.nd.best = c.take<unsigned long long>(nnode);
   w.nd.age = c.take<uint64_t>(nnode);
+  w.nd.immortal = kNone;
   w.dir = c.take<uint32_t>(kDirBuckets + 1);
   w.nclaim = 6 * nvert;
   w.claim = c.take<uint32_t>(w.nclaim);
@@ -879,6 +901,7 @@ int launch_diagram(const float* f, const uint32_t* order, const uint8_t* desc, c
     walk_each<<<nb(nc[1]), TB, 0, s>>>(wk, nullptr, nc[1], w.T0, dstatus); count_launch();
     link_walks<<<nb(nc[1]), TB, 0, s>>>(nc[1], w.T0, w.live0, w.ctr + 0, dstatus); count_launch();
   }
+  w.nd.immortal = kNone;  // every minimum but the global one can die
   int st = run_rounds(w, w.T0, s, dstatus);
   if (st) return st;
   st = write_diagram(0, w, D, f, order, crit0, crit1, nc[1], d0, cap0, n_out + 0, dstatus, s);
@@ -896,6 +919,7 @@ int launch_diagram(const float* f, const uint32_t* order, const uint8_t* desc, c
     walk_each<<<nb(nc[2]), TB, 0, s>>>(wk, nullptr, nc[2], w.T2, dstatus); count_launch();
     link_walks<<<nb(nc[2]), TB, 0, s>>>(nc[2], w.T2, w.live0, w.ctr + 0, dstatus); count_launch();
   }
+  w.nd.immortal = 0;  // OUTSIDE
   st = run_rounds(w, w.T2, s, dstatus);
   if (st) return st;
   st = write_diagram(2, w, D, f, order, crit2, crit3, nc[2], d2, cap2, n_out + 1, dstatus, s);
@@ -1347,6 +1371,7 @@ int launch_diagram_batch(const float* f, const uint32_t* order, const uint8_t* d
     walk_each<<<G * 2, TB, 0, s>>>(wk, cnt_dev + 1, 0, w.T0, dstatus); count_launch();
   }
   b_link_walks<<<G, TB, 0, s>>>(cnt_dev + 1, w.T0, w.live0, w.ctr + 0, dstatus); count_launch();
+  w.nd.immortal = kNone;
   rounds(w.T0);
   write(0, w.T0, crit[0], crit[1], cnt_dev + 1, d0, pair_offsets, pair_totals + 0, fcount);
 
@@ -1362,6 +1387,7 @@ int launch_diagram_batch(const float* f, const uint32_t* order, const uint8_t* d
     walk_each<<<G * 2, TB, 0, s>>>(wk, cnt_dev + 2, 0, w.T2, dstatus); count_launch();
   }
   b_link_walks<<<G, TB, 0, s>>>(cnt_dev + 2, w.T2, w.live0, w.ctr + 0, dstatus); count_launch();
+  w.nd.immortal = 0;  // OUTSIDE, shared by all fields
   rounds(w.T2);
   write(2, w.T2, crit[2], crit[3], cnt_dev + 2, d2, pair_offsets + (nfields + 1), pair_totals + 1,
         fcount + (nfields + 1));

@@ -115,8 +115,9 @@ int check_fields(const dms_field_desc* fh, int nfields, int64_t* total) {
 bool check_caps(const int64_t* caps, int64_t cap_pairs) {
   for (int k = 0; k < 4; ++k)
     if (caps[k] < 0 || caps[k] >= 4294967295ll) return false;
-  // two walks per saddle, 31-bit walk ids
+  // two walks per saddle, 31-bit walk ids and extremum ids
   if (caps[1] >= (1ll << 30) || caps[2] >= (1ll << 30)) return false;
+  if (caps[0] >= (1ll << 31) - 1 || caps[3] >= (1ll << 31) - 2) return false;
   return cap_pairs >= 0;
 }
 

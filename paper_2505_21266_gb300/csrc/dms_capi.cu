@@ -120,8 +120,9 @@ int dms_diagram_d0d2(const float* f, const uint32_t* order, const uint8_t* desc,
     if (n_crit[k] > 0 && !lists[k]) return DMS_ERR_NULL;
   }
   if (n_crit[0] < 1) return DMS_ERR_ARG;  // a grid always has a minimum
-  // 31-bit ids of the two walks per saddle
+  // 31-bit ids of the two walks per saddle and of the extrema
   if (n_crit[1] >= (1ll << 30) || n_crit[2] >= (1ll << 30)) return DMS_ERR_ARG;
+  if (n_crit[0] >= (1ll << 31) - 1 || n_crit[3] >= (1ll << 31) - 2) return DMS_ERR_ARG;
   if (cap0 < 0 || cap2 < 0 || (cap0 > 0 && !d0) || (cap2 > 0 && !d2)) return DMS_ERR_ARG;
   if (ws_bytes < dms::diagram_workspace_bytes(g, n_crit)) return DMS_ERR_WORKSPACE;
   return dms::launch_diagram(f, order, desc, rec, g, crit0, crit1, crit2, crit3, n_crit, d0, cap0,

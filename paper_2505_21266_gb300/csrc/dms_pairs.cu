@@ -147,8 +147,20 @@ __device__ __forceinline__ int tet_type(int c1, int c2) { return cTetTypeOf[c1][
 constexpr uint32_t kLinkBit = 0x80000000u;
 constexpr uint32_t kUnclaimed = 0xFFFFFFFFu;
 
-__device__ __forceinline__ int64_t dir_find_fwd(const int64_t* list, const uint32_t* start,
-                                                int shift, int64_t id);
+// Before the walks, every end (minimum, critical tet) holds an end mark,
+// kLinkBit | its node, in its claim word; a walk's claim fails there and the
+// walk ends with that node, without a search of the critical list.  A
+// claim word thus holds a walk id (a walk passed) or an end mark, and a walk
+// that fails a claim records old ^ kLinkBit: a link to that walk, or the node.
+__device__ __forceinline__ uint32_t claim_result(uint32_t old) { return old ^ kLinkBit; }
+
+__global__ void mark_ends(const int64_t* __restrict__ list, const int64_t* n_dev, int64_t n_host,
+                          uint32_t node0, uint32_t* claim) {
+  const int64_t n = n_dev ? *n_dev : n_host;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    claim[list[i]] = kLinkBit | (uint32_t)(i + node0);
+}
 
 // the node a walk ends at, following the walks it joined
 __device__ __forceinline__ uint32_t resolve_walk(const Sad* __restrict__ sd, uint32_t x,
@@ -162,55 +174,6 @@ __device__ __forceinline__ uint32_t resolve_walk(const Sad* __restrict__ sd, uin
     return 0;
   }
   return x;
-}
-
-__device__ __forceinline__ int64_t bsearch(const int64_t* __restrict__ a, int64_t lo, int64_t hi,
-                                           int64_t key) {
-  const int64_t end = hi;
-  while (lo < hi) {
-    int64_t mid = (lo + hi) >> 1;
-    if (__ldg(a + mid) < key) lo = mid + 1;
-    else hi = mid;
-  }
-  return (lo < end && __ldg(a + lo) == key) ? lo : -1;
-}
-
-// Position of an id in a sorted id list through a directory of bucket starts
-// (bucket = id >> shift, kDirBuckets buckets; the directory stays in L2), so a
-// lookup is a short binary search inside one bucket.
-constexpr int kDirLog = 20;
-constexpr int64_t kDirBuckets = 1ll << kDirLog;
-
-struct Dir {
-  const int64_t* list;
-  int64_t n;
-  const uint32_t* start;  // kDirBuckets + 1 entries
-  int shift;
-};
-
-__global__ void build_dir(const int64_t* __restrict__ list, int64_t n, int shift, uint32_t* start) {
-  int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (b > kDirBuckets) return;
-  const int64_t key = b << shift;
-  int64_t lo = 0, hi = n;
-  while (lo < hi) {
-    int64_t mid = (lo + hi) >> 1;
-    if (list[mid] < key) lo = mid + 1;
-    else hi = mid;
-  }
-  start[b] = (uint32_t)lo;
-}
-
-__device__ __forceinline__ int64_t dir_find_fwd(const int64_t* list, const uint32_t* start,
-                                                int shift, int64_t id) {
-  const int64_t b = id >> shift;
-  return bsearch(list, __ldg(start + b), __ldg(start + b + 1), id);
-}
-
-inline int dir_shift(int64_t max_id) {
-  int bits = 0;
-  while (bits < 62 && (1ll << bits) <= max_id) ++bits;
-  return bits > kDirLog ? bits - kDirLog : 0;
 }
 
 __device__ __forceinline__ void append(uint32_t* list, unsigned int* count, uint32_t v) {
@@ -349,7 +312,6 @@ struct DescWalk {
   F fields;
   const int64_t* crit1;
   const uint8_t* desc;
-  Dir dir0;
   uint32_t* claim;
   struct State {
     Grid g;
@@ -367,22 +329,20 @@ struct DescWalk {
     (void)r;
     return true;
   }
-  // one step; false when the walk has ended with result r
-  // the gradient load and the claim of the current vertex are independent,
-  // so both are in flight together (a minimum may be claimed too: a walk
-  // that meets it there takes the claiming walk's end, the same minimum)
+  // one step; false when the walk has ended with result r.  The gradient
+  // load and the claim of the current vertex are in flight together; the
+  // minima carry end marks, so a walk learns its end from the failed claim
   __device__ __forceinline__ bool step(State& st, uint32_t w, uint32_t& r,
                                        int32_t* dstatus) const {
     const uint8_t d = __ldg(desc + st.v);
     const uint32_t old = atomicCAS(claim + st.v, kUnclaimed, w);
     if (old != kUnclaimed) {
-      r = kLinkBit | old;
+      r = claim_result(old);
       return false;
     }
-    if (d >= 14) {
-      const int64_t pos = dir_find_fwd(dir0.list, dir0.start, dir0.shift, st.v);
-      if (pos < 0) set_status(dstatus, DMS_ERR_ARG);
-      r = pos < 0 ? 0u : (uint32_t)pos;
+    if (d >= 14) {  // a minimum without its end mark: inconsistent input
+      set_status(dstatus, DMS_ERR_ARG);
+      r = 0;
       return false;
     }
     st.v += slot_delta_g(st.g, d);
@@ -402,7 +362,6 @@ struct DualWalk {
   F fields;
   const int64_t* crit2;
   const uint64_t* rec;
-  Dir dir3;
   uint32_t* claim;
   struct State {
     Grid g;
@@ -430,25 +389,18 @@ struct DualWalk {
     st.it = 0;
     return true;
   }
-  // record load and claim in flight together, as for the descending walks
-  // (a critical tet may be claimed: the walks that meet it there take the
-  // claiming walk's end, that tet)
+  // record load and claim in flight together, as for the descending walks;
+  // the critical tets carry end marks
   __device__ __forceinline__ bool step(State& st, uint32_t w, uint32_t& r,
                                        int32_t* dstatus) const {
     const uint64_t rw = __ldg(rec + st.b);
     const uint32_t old = atomicCAS(claim + st.b * 6 + st.k, kUnclaimed, w);
     if (old != kUnclaimed) {
-      r = kLinkBit | old;
+      r = claim_result(old);
       return false;
     }
     const uint32_t code = (uint32_t)(rw >> (33 + 3 * st.k)) & 7u;
-    if (code == 7u) {
-      const int64_t pos = dir_find_fwd(dir3.list, dir3.start, dir3.shift, st.b * 6 + st.k);
-      if (pos < 0) set_status(dstatus, DMS_ERR_ARG);
-      r = pos < 0 ? 0u : (uint32_t)pos + 1;
-      return false;
-    }
-    if (code < 1u || code > 4u) {
+    if (code < 1u || code > 4u) {  // a critical tet without its end mark, or bad data
       set_status(dstatus, DMS_ERR_ARG);
       r = 0;
       return false;
@@ -608,6 +560,10 @@ __global__ void round_merge(const uint32_t* __restrict__ live, const unsigned in
     unsigned long long tv = (round << 44) | (kMask44 - T.s[i].w);
     const bool la = a != nd.immortal && nd.best[a] == tv;
     const bool lb = b != nd.immortal && nd.best[b] == tv;
+    if (!la && !lb) {  // the lightest live saddle of neither side: wait
+      append(next, next_n, i);
+      continue;
+    }
     const uint64_t ga = nd.age[a], gb = nd.age[b];
     uint32_t young = kNone, old = kNone;
     if (la && lb) {
@@ -783,7 +739,6 @@ struct DiagWs {
   uint32_t *live0, *live1;
   unsigned int* ctr;  // [0..1] live counts, [2] pair count
   Nodes nd;  // union-find nodes: parent, best live saddle, age
-  uint32_t* dir;  // kDirBuckets + 1 bucket starts
   uint32_t* claim;  // one word per tet id: the dual walk that passed it
   int64_t nclaim;
   radix64::Buffers rb;
@@ -805,7 +760,6 @@ DiagWs carve_diag(void* base, const int64_t* nc, int64_t nvert) {
   w.nd.best = c.take<unsigned long long>(nnode);
   w.nd.age = c.take<uint64_t>(nnode);
   w.nd.immortal = kNone;
-  w.dir = c.take<uint32_t>(kDirBuckets + 1);
   w.nclaim = 6 * nvert;
   w.claim = c.take<uint32_t>(w.nclaim);
   w.rb = radix64::carve(c, std::max<int64_t>(nsad, 4096));
@@ -893,11 +847,10 @@ int launch_diagram(const float* f, const uint32_t* order, const uint8_t* desc, c
     write_essential<<<nb(nc[0]), TB, 0, s>>>(f, order, crit0, nc[0], ess); count_launch();
   }
   if (nc[1] > 0) {
-    Dir d0dir{crit0, nc[0], w.dir, dir_shift(g.n)};
-    build_dir<<<nb(kDirBuckets + 1), TB, 0, s>>>(crit0, nc[0], d0dir.shift, w.dir); count_launch();
     DMS_CUDA_OK(cudaMemsetAsync(w.claim, 0xFF, g.n * sizeof(uint32_t), s));
+    mark_ends<<<nb(nc[0]), TB, 0, s>>>(crit0, nullptr, nc[0], 0, w.claim); count_launch();
     d0_weights<<<nb(nc[1]), TB, 0, s>>>(D, order, crit1, nc[1], w.T0); count_launch();
-    const DescWalk<OneField> wk{OneField{g}, crit1, desc, d0dir, w.claim};
+    const DescWalk<OneField> wk{OneField{g}, crit1, desc, w.claim};
     walk_each<<<nb(nc[1]), TB, 0, s>>>(wk, nullptr, nc[1], w.T0, dstatus); count_launch();
     link_walks<<<nb(nc[1]), TB, 0, s>>>(nc[1], w.T0, w.live0, w.ctr + 0, dstatus); count_launch();
   }
@@ -911,11 +864,12 @@ int launch_diagram(const float* f, const uint32_t* order, const uint8_t* desc, c
   DMS_CUDA_OK(cudaMemsetAsync(w.ctr, 0, 8 * sizeof(unsigned int), s));
   init_nodes_d2<<<nb(nc[3] + 1), TB, 0, s>>>(D, order, crit3, nc[3], w.nd); count_launch();
   if (nc[2] > 0) {
-    Dir d3dir{crit3, nc[3], w.dir, dir_shift(6 * g.n)};
-    build_dir<<<nb(kDirBuckets + 1), TB, 0, s>>>(crit3, nc[3], d3dir.shift, w.dir); count_launch();
     DMS_CUDA_OK(cudaMemsetAsync(w.claim, 0xFF, w.nclaim * sizeof(uint32_t), s));
+    if (nc[3] > 0) {
+      mark_ends<<<nb(nc[3]), TB, 0, s>>>(crit3, nullptr, nc[3], 1, w.claim); count_launch();
+    }
     d2_weights<<<nb(nc[2]), TB, 0, s>>>(D, order, crit2, nc[2], w.T2); count_launch();
-    const DualWalk<OneField> wk{OneField{g}, crit2, rec, d3dir, w.claim};
+    const DualWalk<OneField> wk{OneField{g}, crit2, rec, w.claim};
     walk_each<<<nb(nc[2]), TB, 0, s>>>(wk, nullptr, nc[2], w.T2, dstatus); count_launch();
     link_walks<<<nb(nc[2]), TB, 0, s>>>(nc[2], w.T2, w.live0, w.ctr + 0, dstatus); count_launch();
   }
@@ -989,20 +943,6 @@ __device__ __forceinline__ uint32_t local_rank_f(const Grid& g, int64_t off,
     r += __ldg(order + t + slot_delta_of(g, s)) < ou ? 1u : 0u;
   }
   return r;
-}
-
-__global__ void b_build_dir(const int64_t* __restrict__ list, const int64_t* __restrict__ n_dev,
-                            int shift, uint32_t* start) {
-  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (b > kDirBuckets) return;
-  const int64_t key = b << shift;
-  int64_t lo = 0, hi = *n_dev;
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (list[mid] < key) lo = mid + 1;
-    else hi = mid;
-  }
-  start[b] = (uint32_t)lo;
 }
 
 __global__ void b_init_nodes_d0(const uint32_t* __restrict__ order, const int64_t* __restrict__ crit0,
@@ -1329,8 +1269,6 @@ int launch_diagram_batch(const float* f, const uint32_t* order, const uint8_t* d
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const unsigned G = (unsigned)sms * 8, TB = 256;  // grid-stride launches
-  const unsigned dir_blocks = (unsigned)((kDirBuckets + TB) / TB);
-  const int shift0 = dir_shift(total_vertices), shift3 = dir_shift(6 * total_vertices);
   DMS_CUDA_OK(cudaMemsetAsync(fcount, 0, 2 * (nfields + 1) * sizeof(unsigned long long), s));
 
   bool mem_ok = true;
@@ -1362,12 +1300,11 @@ int launch_diagram_batch(const float* f, const uint32_t* order, const uint8_t* d
   DMS_CUDA_OK(cudaMemsetAsync(w.ctr, 0, 8 * sizeof(unsigned int), s));
   b_init_nodes_d0<<<G, TB, 0, s>>>(order, crit[0], cnt_dev, w.nd); count_launch();
   b_essential<<<G, TB, 0, s>>>(ft, f, order, crit[0], cnt_dev, ess); count_launch();
-  b_build_dir<<<dir_blocks, TB, 0, s>>>(crit[0], cnt_dev + 0, shift0, w.dir); count_launch();
-  const Dir dir0{crit[0], caps[0], w.dir, shift0};
   DMS_CUDA_OK(cudaMemsetAsync(w.claim, 0xFF, total_vertices * sizeof(uint32_t), s));
+  mark_ends<<<G, TB, 0, s>>>(crit[0], cnt_dev + 0, 0, 0, w.claim); count_launch();
   b_d0_weights<<<G, TB, 0, s>>>(ft, order, crit[1], cnt_dev, w.T0); count_launch();
   {
-    const DescWalk<ManyFields> wk{ManyFields{fields_dev, nfields}, crit[1], desc, dir0, w.claim};
+    const DescWalk<ManyFields> wk{ManyFields{fields_dev, nfields}, crit[1], desc, w.claim};
     walk_each<<<G * 2, TB, 0, s>>>(wk, cnt_dev + 1, 0, w.T0, dstatus); count_launch();
   }
   b_link_walks<<<G, TB, 0, s>>>(cnt_dev + 1, w.T0, w.live0, w.ctr + 0, dstatus); count_launch();
@@ -1378,12 +1315,11 @@ int launch_diagram_batch(const float* f, const uint32_t* order, const uint8_t* d
   // ---- D2
   DMS_CUDA_OK(cudaMemsetAsync(w.ctr, 0, 8 * sizeof(unsigned int), s));
   b_init_nodes_d2<<<G, TB, 0, s>>>(ft, order, crit[3], cnt_dev, w.nd); count_launch();
-  b_build_dir<<<dir_blocks, TB, 0, s>>>(crit[3], cnt_dev + 3, shift3, w.dir); count_launch();
-  const Dir dir3{crit[3], caps[3], w.dir, shift3};
   DMS_CUDA_OK(cudaMemsetAsync(w.claim, 0xFF, w.nclaim * sizeof(uint32_t), s));
+  mark_ends<<<G, TB, 0, s>>>(crit[3], cnt_dev + 3, 0, 1, w.claim); count_launch();
   b_d2_weights<<<G, TB, 0, s>>>(ft, order, crit[2], cnt_dev, w.T2); count_launch();
   {
-    const DualWalk<ManyFields> wk{ManyFields{fields_dev, nfields}, crit[2], rec, dir3, w.claim};
+    const DualWalk<ManyFields> wk{ManyFields{fields_dev, nfields}, crit[2], rec, w.claim};
     walk_each<<<G * 2, TB, 0, s>>>(wk, cnt_dev + 2, 0, w.T2, dstatus); count_launch();
   }
   b_link_walks<<<G, TB, 0, s>>>(cnt_dev + 2, w.T2, w.live0, w.ctr + 0, dstatus); count_launch();

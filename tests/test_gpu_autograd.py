@@ -133,3 +133,21 @@ def test_backward_kernel_scatter():
     expect[5] += 2.0 + 3.0 + 4.0
     expect[2] += 5.0
     assert np.array_equal(grad.cpu().numpy().ravel(), expect)
+
+
+def test_descent_loop_at_128_cubed():
+    """The differentiable workload: a 128^3 mixture of 32 Gaussians plus
+    U[0, 1e-4), 100 gradient-descent steps at lr 1e-2 on the topological
+    loss, the diagram recomputed at every step.  The loss must fall well
+    below its start, and every step's loss must be finite."""
+    f = fields.config4(0, "cuda")
+    losses = []
+    for _ in range(100):
+        x = f.clone().requires_grad_(True)
+        loss = dms.topological_loss(x, THRESH)
+        loss.backward()
+        losses.append(float(loss.item()))
+        f = (x - 1e-2 * x.grad).detach()
+    assert all(np.isfinite(losses))
+    assert losses[0] > 0
+    assert losses[-1] < 0.5 * losses[0]

@@ -41,10 +41,15 @@ constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint64_t kMask44 = (1ull << 44) - 1;
 constexpr int kCornerOfEdge[7] = {1, 2, 4, 3, 5, 6, 7};
 
-__constant__ int cCornerOfEdge[7] = {1, 2, 4, 3, 5, 6, 7};
-__constant__ int cTriPQ[12][2] = {{1, 3}, {2, 3}, {1, 5}, {4, 5}, {2, 6}, {4, 6},
-                                  {1, 7}, {2, 7}, {4, 7}, {3, 7}, {5, 7}, {6, 7}};
-__constant__ int cTetC[6][2] = {{1, 3}, {1, 5}, {2, 3}, {2, 6}, {4, 5}, {4, 6}};
+// The type tables (corners of edge type k, triangle type k = (p, q), tet type
+// k = chain (c1, c2)) as 4-bit fields of immediates: a lookup with an index
+// that differs between lanes is a shift and a mask, not a serialised
+// constant-memory access.
+__device__ __forceinline__ int edge_corner(int k) { return (0x7653421u >> (4 * k)) & 15; }
+__device__ __forceinline__ int tri_p(int k) { return (int)((0x653421424121ull >> (4 * k)) & 15); }
+__device__ __forceinline__ int tri_q(int k) { return (int)((0x777777665533ull >> (4 * k)) & 15); }
+__device__ __forceinline__ int tet_c1(int k) { return (0x442211u >> (4 * k)) & 15; }
+__device__ __forceinline__ int tet_c2(int k) { return (0x656353u >> (4 * k)) & 15; }
 // neighbour slots: +c for s < 7, -c for s >= 7, c = corner of edge type s % 7
 __constant__ int cSlotCorner[14] = {1, 2, 4, 3, 5, 6, 7, 1, 2, 4, 3, 5, 6, 7};
 
@@ -131,14 +136,12 @@ __device__ __forceinline__ void local_rank2(const Dev& D, const uint32_t* __rest
   }
 }
 
-// tet type of the chain 0 < c1 < c2 < 7 (index [c1][c2]), -1 if none
-__constant__ signed char cTetTypeOf[8][8] = {
-    {-1, -1, -1, -1, -1, -1, -1, -1}, {-1, -1, -1, 0, -1, 1, -1, -1},
-    {-1, -1, -1, 2, -1, -1, 3, -1},   {-1, -1, -1, -1, -1, -1, -1, -1},
-    {-1, -1, -1, -1, -1, 4, 5, -1},   {-1, -1, -1, -1, -1, -1, -1, -1},
-    {-1, -1, -1, -1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1, -1, -1, -1}};
-
-__device__ __forceinline__ int tet_type(int c1, int c2) { return cTetTypeOf[c1][c2]; }
+// tet type of the chain 0 < c1 < c2 < 7 (c1 one corner bit, c2 two): the
+// types are ordered by c1, then by whether the bit c2 adds is the larger of
+// the two bits c1 leaves
+__device__ __forceinline__ int tet_type(int c1, int c2) {
+  return (c1 >> 1) * 2 + ((c2 ^ c1) > (7 ^ c2) ? 1 : 0);
+}
 
 // Walks with path sharing: every vertex (D0) or non-critical tet (D2) a walk
 // passes is claimed for it (atomicCAS on claim[id]); a walk that reaches an id
@@ -195,7 +198,7 @@ __global__ void d0_weights(Dev D, const uint32_t* __restrict__ order,
   int64_t id = crit1[i];
   int64_t a = id / 7;
   int k = (int)(id - a * 7);
-  int64_t b = a + corner_delta(D.g, cCornerOfEdge[k]);
+  int64_t b = a + corner_delta(D.g, edge_corner(k));
   uint32_t oa = __ldg(order + a), ob = __ldg(order + b);
   int64_t top = oa > ob ? a : b;
   uint32_t r = local_rank(D, order, top, oa > ob ? ob : oa);
@@ -207,7 +210,7 @@ __global__ void d0_weights(Dev D, const uint32_t* __restrict__ order,
 // (anchor coordinates ax, ay, az); -1 where a cofacet leaves the grid.
 __device__ __forceinline__ void tri_cofacets(const Grid& g, int64_t a, int k, int64_t ax,
                                              int64_t ay, int64_t az, int64_t cof[2]) {
-  const int p = cTriPQ[k][0], q = cTriPQ[k][1];
+  const int p = tri_p(k), q = tri_q(k);
   cof[0] = cof[1] = -1;
   if (q == 7) {
     const int e = (__popc(p) == 1) ? (7 ^ p) : p;
@@ -237,7 +240,7 @@ __global__ void d2_weights(Dev D, const uint32_t* __restrict__ order,
   int64_t id = crit2[i];
   int64_t a = id / 12;
   int k = (int)(id - a * 12);
-  const int p = cTriPQ[k][0], q = cTriPQ[k][1];
+  const int p = tri_p(k), q = tri_q(k);
   int64_t v[3] = {a, a + corner_delta(D.g, p), a + corner_delta(D.g, q)};
   uint32_t o[3] = {__ldg(order + v[0]), __ldg(order + v[1]), __ldg(order + v[2])};
   int it = 0;
@@ -324,7 +327,7 @@ struct DescWalk {
     const int k = (int)(id - a * 7);
     int64_t off;
     fields.get(a, st.g, off);
-    st.v = j ? a + corner_delta(st.g, cCornerOfEdge[k]) : a;
+    st.v = j ? a + corner_delta(st.g, edge_corner(k)) : a;
     st.it = 0;
     (void)r;
     return true;
@@ -405,7 +408,7 @@ struct DualWalk {
       r = 0;
       return false;
     }
-    const int c1 = cTetC[st.k][0], c2 = cTetC[st.k][1];
+    const int c1 = tet_c1(st.k), c2 = tet_c2(st.k);
     int n1, n2, stp = 0, sg = 0;
     switch (code - 1) {
       case 0: stp = c1; sg = 1; n1 = c2 ^ c1; n2 = 7 ^ c1; break;    // omits the anchor
@@ -491,7 +494,7 @@ __global__ void init_nodes_d2(Dev D, const uint32_t* __restrict__ order,
   int64_t id = crit3[i - 1];
   int64_t a = id / 6;
   int k = (int)(id - a * 6);
-  int cs[4] = {0, cTetC[k][0], cTetC[k][1], 7};
+  int cs[4] = {0, tet_c1(k), tet_c2(k), 7};
   int64_t v[4];
   uint32_t o[4];
   int it = 0;
@@ -651,7 +654,7 @@ __device__ __forceinline__ void write_one_d0(const Dev& D, const float* f, const
   int64_t id = crit1[i];
   int64_t a = id / 7;
   int k = (int)(id - a * 7);
-  int64_t v[2] = {a, a + corner_delta(D.g, cCornerOfEdge[k])};
+  int64_t v[2] = {a, a + corner_delta(D.g, edge_corner(k))};
   int64_t top = top_of(D, order, v, 2);
   dms_pair p;
   p.birth_id = m;
@@ -670,10 +673,10 @@ __device__ __forceinline__ void write_one_d2(const Dev& D, const float* f, const
   int64_t tri = crit2[i];
   int64_t a = tri / 12;
   int k = (int)(tri - a * 12);
-  int64_t tv[3] = {a, a + corner_delta(D.g, cTriPQ[k][0]), a + corner_delta(D.g, cTriPQ[k][1])};
+  int64_t tv[3] = {a, a + corner_delta(D.g, tri_p(k)), a + corner_delta(D.g, tri_q(k))};
   int64_t b = tet / 6;
   int kk = (int)(tet - b * 6);
-  int64_t qv[4] = {b, b + corner_delta(D.g, cTetC[kk][0]), b + corner_delta(D.g, cTetC[kk][1]),
+  int64_t qv[4] = {b, b + corner_delta(D.g, tet_c1(kk)), b + corner_delta(D.g, tet_c2(kk)),
                    b + corner_delta(D.g, 7)};
   int64_t st = top_of(D, order, tv, 3), qt = top_of(D, order, qv, 4);
   dms_pair p;
@@ -988,7 +991,7 @@ __global__ void b_d0_weights(const FieldTab ft, const uint32_t* __restrict__ ord
     const int k = (int)(id - a * 7);
     const dms_field_desc fd = ft.fd[field_of_vertex(ft, a)];
     const Grid g = grid_of(fd);
-    const int64_t b = a + corner_delta(g, cCornerOfEdge[k]);
+    const int64_t b = a + corner_delta(g, edge_corner(k));
     const uint32_t oa = __ldg(order + a), ob = __ldg(order + b);
     const int64_t top = oa > ob ? a : b;
     const uint32_t r = local_rank_f(g, fd.offset, order, top, oa > ob ? ob : oa);
@@ -1014,7 +1017,7 @@ __global__ void b_init_nodes_d2(const FieldTab ft, const uint32_t* __restrict__ 
     const int k = (int)(id - a * 6);
     const dms_field_desc fd = ft.fd[field_of_vertex(ft, a)];
     const Grid g = grid_of(fd);
-    const int cs[4] = {0, cTetC[k][0], cTetC[k][1], 7};
+    const int cs[4] = {0, tet_c1(k), tet_c2(k), 7};
     int64_t v[4];
     uint32_t o[4];
     int it = 0;
@@ -1045,7 +1048,7 @@ __global__ void b_d2_weights(const FieldTab ft, const uint32_t* __restrict__ ord
     const int k = (int)(id - a * 12);
     const dms_field_desc fd = ft.fd[field_of_vertex(ft, a)];
     const Grid g = grid_of(fd);
-    const int p = cTriPQ[k][0], q = cTriPQ[k][1];
+    const int p = tri_p(k), q = tri_q(k);
     int64_t v[3] = {a, a + corner_delta(g, p), a + corner_delta(g, q)};
     uint32_t o[3] = {__ldg(order + v[0]), __ldg(order + v[1]), __ldg(order + v[2])};
     int it = 0;
@@ -1198,7 +1201,7 @@ __global__ void __launch_bounds__(PNT) b_write_pairs(int dim, const FieldTab ft,
         const int kk = (int)(id - a * 7);
         const dms_field_desc fd = ft.fd[field_of_vertex(ft, a)];
         const Grid g = grid_of(fd);
-        int64_t v[2] = {a, a + corner_delta(g, cCornerOfEdge[kk])};
+        int64_t v[2] = {a, a + corner_delta(g, edge_corner(kk))};
         const int64_t top = top_of(Dev{}, order, v, 2);
         p.birth_id = m - fd.offset;
         p.death_id = id - 7 * fd.offset;
@@ -1213,10 +1216,10 @@ __global__ void __launch_bounds__(PNT) b_write_pairs(int dim, const FieldTab ft,
         const int kk = (int)(tri - a * 12);
         const dms_field_desc fd = ft.fd[field_of_vertex(ft, a)];
         const Grid g = grid_of(fd);
-        int64_t tv[3] = {a, a + corner_delta(g, cTriPQ[kk][0]), a + corner_delta(g, cTriPQ[kk][1])};
+        int64_t tv[3] = {a, a + corner_delta(g, tri_p(kk)), a + corner_delta(g, tri_q(kk))};
         const int64_t b = tet / 6;
         const int kq = (int)(tet - b * 6);
-        int64_t qv[4] = {b, b + corner_delta(g, cTetC[kq][0]), b + corner_delta(g, cTetC[kq][1]),
+        int64_t qv[4] = {b, b + corner_delta(g, tet_c1(kq)), b + corner_delta(g, tet_c2(kq)),
                          b + corner_delta(g, 7)};
         const int64_t st = top_of(Dev{}, order, tv, 3), qt = top_of(Dev{}, order, qv, 4);
         p.birth_id = tri - 12 * fd.offset;

@@ -138,6 +138,24 @@ def cpu_baseline(field_np: np.ndarray, crop: int):
                       f"of the workload field, {dt:.1f} s"}
 
 
+def whole_job(ms_local: float, units_local: int, steps: int, device=None):
+    """Whole-job throughput of N replicas: the units all ranks processed over
+    the slowest rank's time (every rank calls this; N = 1 needs no process
+    group).  Returns (units per second, the max time in ms)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return units_local * steps / (ms_local / 1e3), ms_local
+    t = torch.tensor([ms_local, float(units_local)], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    tsum = t.clone()
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    dist.barrier()
+    ms = float(tmax[0].item())
+    return float(tsum[1].item()) * steps / (ms / 1e3), ms
+
+
 def bench_batched(dev, steps: int, warmup: int):
     """256 fields of uneven dims (each axis U{32..256}; even fields Gaussian
     mixtures, odd fields U[0,1)), all resident in HBM: one batched launch
@@ -364,12 +382,7 @@ def main():
     clocks = sampler.stop()
     ms = t_start.elapsed_time(t_end)
     grad_ms = statistics.mean(a.elapsed_time(b) for a, b in gev)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
-    value = nvert * world * args.steps / (ms / 1e3)
+    value, ms = whole_job(ms, nvert, args.steps, dev)
 
     # end to end through the public API, the field coming from pinned host memory
     e2e = None
@@ -418,13 +431,14 @@ def main():
         "clocks": clocks,
         "e2e": e2e,
     }
-    if rank == 0 and not args.no_cpu_baseline:
+    # the CPU baseline and the single-GPU comparison legs belong to the N = 1 line
+    if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(f.cpu().numpy(), args.crop)
     del f, d, c
     torch.cuda.empty_cache()
-    if not args.no_batched:
+    if world == 1 and not args.no_batched:
         line["batched"] = bench_batched(dev, args.steps, args.warmup)
-    if not args.no_diff:
+    if world == 1 and not args.no_diff:
         line["differentiable"] = bench_differentiable(dev, args.steps, args.warmup)
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -22,6 +22,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "dms_oracle.cpp")
+_SRC2 = os.path.join(_HERE, "dms_oracle2d.cpp")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "libdms_oracle.so")
 _lock = threading.Lock()
@@ -44,11 +45,12 @@ def build(force: bool = False) -> str:
     """Compile the oracle with g++ (plain C++17, -O2, no OpenMP)."""
     with _lock:
         if (not force and os.path.exists(_LIB)
-                and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+                and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC), os.path.getmtime(_SRC2))):
             return _LIB
         os.makedirs(_BUILD, exist_ok=True)
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", _SRC, "-o", tmp])
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", _SRC, _SRC2,
+                               "-o", tmp])
         os.replace(tmp, _LIB)
         return _LIB
 
@@ -72,6 +74,16 @@ def _load():
         lib.orc_pair_extrema_saddles.argtypes = [i64, vp, vp, i64, vp, vp]
         lib.orc_lower_star_vertex.restype = ctypes.c_int
         lib.orc_lower_star_vertex.argtypes = [vp, i64, i64, i64, i64, vp, i64, vp, vp, i64, vp]
+        lib.orc2_run.restype = vp
+        lib.orc2_run.argtypes = [vp, i64, i64, ctypes.c_int]
+        lib.orc2_status.restype = ctypes.c_int
+        lib.orc2_status.argtypes = [vp]
+        lib.orc2_count.restype = i64
+        lib.orc2_count.argtypes = [vp, ctypes.c_int]
+        lib.orc2_copy.restype = None
+        lib.orc2_copy.argtypes = [vp, ctypes.c_int, vp]
+        lib.orc2_free.restype = None
+        lib.orc2_free.argtypes = [vp]
         for name in ("orc_d0_edge_local", "orc_d2_triangle_local"):
             fn = getattr(lib, name)
             fn.restype = ctypes.c_int
@@ -191,3 +203,60 @@ def d2_triangle_local(field: np.ndarray, tri: int, limit: int = 1 << 62):
     """Dual elder rule at one triangle on tetrahedra + the outside:
     (1, dying tetrahedron), (0, -3) or (-1, -3) as in d0_edge_local."""
     return _local("orc_d2_triangle_local", field, tri, limit)
+
+
+# ---------------------------------------------------------------- 2D grids --
+# selectors of orc2_copy (mirror the enum in dms_oracle2d.cpp)
+ORDER2, CRIT2_0, CRIT2_1, CRIT2_2, GRAD_PAIRS2, D0_2, D1_2, D0_ESSENTIAL2, REDUCTION2 = range(9)
+
+
+class Result2:
+    """Everything the 2D oracle computed for one field [ny, nx]."""
+
+    def __init__(self, field: np.ndarray, flags: int):
+        f = np.ascontiguousarray(field, dtype=np.float32)
+        if f.ndim != 2:
+            raise ValueError("field must be 2D, indexed [y, x]")
+        ny, nx = f.shape
+        lib = _load()
+        self._h = lib.orc2_run(f.ctypes.data, nx, ny, flags)
+        st = lib.orc2_status(self._h)
+        if st:
+            lib.orc2_free(self._h)
+            self._h = None
+            raise OracleError(_STATUS.get(st, f"status {st}"))
+
+    def get(self, what: int) -> np.ndarray:
+        lib = _load()
+        n = lib.orc2_count(self._h, what)
+        if what in (D0_2, D1_2, D0_ESSENTIAL2):
+            out = np.empty(n, dtype=PAIR_DTYPE)
+        elif what == ORDER2:
+            out = np.empty(n, dtype=np.uint32)
+        else:
+            out = np.empty(n, dtype=np.int64)
+        if n:
+            lib.orc2_copy(self._h, what, out.ctypes.data)
+        if what in (GRAD_PAIRS2, REDUCTION2):
+            out = out.reshape(-1, 3)
+        return out
+
+    @property
+    def order(self):
+        return self.get(ORDER2)
+
+    def crit(self, d: int) -> np.ndarray:
+        return self.get(CRIT2_0 + d)
+
+    def __del__(self):
+        if getattr(self, "_h", None) is not None:
+            _load().orc2_free(self._h)
+            self._h = None
+
+
+def run2(field: np.ndarray, diagrams=True, reduction=False) -> Result2:
+    """The 2D oracle on a field indexed [y, x]: order, gradient, critical
+    simplices and (by default) the D0 / D1 pairs; the boundary-matrix
+    reduction on request (small grids only)."""
+    flags = 1 | 2 | (4 if diagrams else 0) | (8 if reduction else 0)
+    return Result2(field, flags)

@@ -421,7 +421,9 @@ def main():
                      "peak": issue_peak, "unit": "Tinst/s (lane-instructions)",
                      "frac": achieved / issue_peak,
                      "peak_kind": f"derived: {sms} SMs x 4 x 32 lanes x {sm_mhz:.0f} MHz",
-                     "traffic": GRAD_DRAM_BYTES_PER_VERTEX * nvert,
+                     # the per-vertex figures were measured on the 1024^3 recipe
+                     "traffic": GRAD_DRAM_BYTES_PER_VERTEX * nvert if args.workload == "c3" else None,
+                     "figures_from": "gradient_kernel on the c3 recipe (profiles/gradient_kernel_c3.md)",
                      "kernel_ms": grad_ms, "warp_inst_per_vertex": GRAD_WARP_INST_PER_VERTEX,
                      "hbm": {"algorithmic_bytes": grad_bytes,
                              "achieved_gbs": grad_bytes / (grad_ms / 1e3) / 1e9,

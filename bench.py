@@ -241,6 +241,33 @@ def bench_differentiable(dev, steps: int, warmup: int):
     return out
 
 
+def bench_2d(dev, steps: int, warmup: int, n: int = 16384):
+    """The 2D path on an n x n field (64 Gaussians, sigma U[0.01,0.1], plus
+    U[0,1e-2)): order, gradient, critical simplices, D0 and D1 -- the whole
+    diagram of a 2D field -- in vertices/s."""
+    import torch
+    import paper_2505_21266_gb300 as dms
+    from paper_2505_21266_gb300 import fields
+    f = fields.gaussian_mixture((1, n, n), 64, (0.01, 0.1), 1e-2, 0, dev)[0].contiguous()
+    for _ in range(warmup):
+        r = dms.diagram2d(f)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        r = dms.diagram2d(f)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    out = {"workload": f"{n}^2 float32, 64 Gaussians (sigma U[0.01,0.1]) + U[0,1e-2)",
+           "vertices": n * n, "ms_per_step": ms, "vertices_per_s": n * n / (ms / 1e3),
+           "critical": [int(c.numel()) for c in r.crit],
+           "pairs_d0_d1": [int(r.diagrams.d0.shape[0]), int(r.diagrams.d1.shape[0])]}
+    del f, r
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args):
     """--impl reference: the oracle on bounded crops of the workload field."""
     rank = int(os.environ.get("RANK", "0"))
@@ -293,6 +320,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-field batch leg")
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiable leg")
+    ap.add_argument("--no-2d", action="store_true", help="skip the 2D leg")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -442,6 +470,8 @@ def main():
         line["batched"] = bench_batched(dev, args.steps, args.warmup)
     if world == 1 and not args.no_diff:
         line["differentiable"] = bench_differentiable(dev, args.steps, args.warmup)
+    if world == 1 and not args.no_2d:
+        line["grid_2d"] = bench_2d(dev, args.steps, args.warmup)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -272,6 +272,53 @@ int dms_batch_diagrams(const float* f, const dms_field_desc* fields_host,
 int dms_backward(const dms_pair* pairs, int64_t n, const float* g, dms_dims d, float* grad,
                  int32_t* dstatus, void* stream);
 
+/* -------------------------------------------------------------------- 2D ---
+ * The same path on a 2D grid (nx x ny, each >= 2, nx*ny < 2^32 - 1), where
+ * the extremum-saddle pairs D0 and D1 are the whole persistence diagram.
+ * Conventions as above, one dimension down: vertex v = x + nx*y; the
+ * Freudenthal split of every square along its (1,1) diagonal; ids (int64)
+ *   vertex v;  edge 3a + k, corner {+x, +y, +x+y}[k];
+ *   triangle 2a + k = {a, a+p, a+(1,1)}, p = {+x, +y}[k].
+ * Neighbour slots of a vertex: s < 3 -> +corner, s >= 3 -> -corner of edge
+ * type s % 3.
+ *
+ * dms2_order -- as dms_order (Sec. 2.1), on nx*ny vertices.
+ * dms2_gradient -- ProcessLowerStars on every vertex (Sec. 2.3):
+ *   desc  [n] uint8 out: 0..5 the slot of the edge v is paired with, 15 a minimum.
+ *   rec   [n] uint16 out, per anchor a: bits 3k..3k+2 edge k (0 = absent or
+ *         paired with its top vertex, 1..2 = paired with the (code-1)-th
+ *         triangle holding it by increasing id on the unbounded lattice,
+ *         7 = critical); bits 9+3k..11+3k triangle k (0 = absent, 1..3 =
+ *         paired with the facet that omits vertex (code-1) of its chain
+ *         a < a+p < a+(1,1), 7 = critical); other bits 0.
+ * dms2_critical -- the critical vertices, edges and triangles in increasing
+ *   id order (caps, counts and errors as dms_critical, three lists).
+ * dms2_diagram_d0d1 -- D0 as in 3D (Alg. 1, minima against edges); D1 by
+ *   the dual walks from the two triangles of every critical edge to a
+ *   critical triangle or OUTSIDE (off the grid), edges taken in decreasing
+ *   order, the lower maximum dying (Alg. 1 on the dual graph).  D0 pairs in
+ *   increasing edge-id order (n_crit[0]-1 of them, plus the essential class),
+ *   D1 pairs (birth = edge, death = triangle) in increasing edge-id order
+ *   (n_crit[2] of them).  n_crit is a HOST array of 3 (n_crit[1] < 2^30).
+ *   Synchronises the stream between pairing rounds, as dms_diagram_d0d2.
+ */
+size_t dms2_order_workspace_size(int32_t nx, int32_t ny);
+int dms2_order(const float* f, int32_t nx, int32_t ny, uint32_t* order, void* ws, size_t ws_bytes,
+               int32_t* dstatus, void* stream);
+int dms2_gradient(const uint32_t* order, int32_t nx, int32_t ny, uint8_t* desc, uint16_t* rec,
+                  void* stream);
+size_t dms2_critical_workspace_size(int32_t nx, int32_t ny);
+int dms2_critical(const uint8_t* desc, const uint16_t* rec, int32_t nx, int32_t ny, int64_t* crit0,
+                  int64_t* crit1, int64_t* crit2, const int64_t* cap, int64_t* counts, void* ws,
+                  size_t ws_bytes, int32_t* dstatus, void* stream);
+size_t dms2_diagram_workspace_size(int32_t nx, int32_t ny, const int64_t* n_crit);
+int dms2_diagram_d0d1(const float* f, const uint32_t* order, const uint8_t* desc,
+                      const uint16_t* rec, int32_t nx, int32_t ny, const int64_t* crit0,
+                      const int64_t* crit1, const int64_t* crit2, const int64_t* n_crit,
+                      dms_pair* d0, int64_t cap0, dms_pair* d1, int64_t cap1,
+                      dms_pair* d0_essential, int64_t* n_out, void* ws, size_t ws_bytes,
+                      int32_t* dstatus, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -46,6 +46,16 @@ SIGNATURES = [
     ("dms_diagram_d0d2", ctypes.c_int,
      [_VP, _VP, _VP, _VP, dms_dims, _VP, _VP, _VP, _VP, _VP, _VP, _I64, _VP, _I64, _VP, _VP,
       _VP, _SZ, _VP, _VP]),
+    ("dms2_order_workspace_size", _SZ, [_I32, _I32]),
+    ("dms2_order", ctypes.c_int, [_VP, _I32, _I32, _VP, _VP, _SZ, _VP, _VP]),
+    ("dms2_gradient", ctypes.c_int, [_VP, _I32, _I32, _VP, _VP, _VP]),
+    ("dms2_critical_workspace_size", _SZ, [_I32, _I32]),
+    ("dms2_critical", ctypes.c_int,
+     [_VP, _VP, _I32, _I32, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP, _VP]),
+    ("dms2_diagram_workspace_size", _SZ, [_I32, _I32, _VP]),
+    ("dms2_diagram_d0d1", ctypes.c_int,
+     [_VP, _VP, _VP, _VP, _I32, _I32, _VP, _VP, _VP, _VP, _VP, _I64, _VP, _I64, _VP, _VP, _VP,
+      _SZ, _VP, _VP]),
     ("dms_batch_tile_variants", _I32, []),
     ("dms_batch_max_rounds", _I32, []),
     ("dms_batch_workspace_size", _SZ, [_VP, _I32, _VP, _I64]),

@@ -259,3 +259,124 @@ def topological_loss(field: torch.Tensor, threshold: float = 0.05) -> torch.Tens
     pers = v[:, 1] - v[:, 0]
     keep = pers < threshold
     return (pers[keep] ** 2).sum()
+
+
+# -------------------------------------------------------------------- 2D --
+
+def dims2_of(field: torch.Tensor):
+    if field.dim() != 2:
+        raise ValueError("a 2D field is a 2D tensor indexed [y, x]")
+    ny, nx = field.shape
+    return int(nx), int(ny)
+
+
+def order2d(field: torch.Tensor, status: torch.Tensor | None = None, check: bool = True):
+    """Global vertex order of a 2D field (Sec. 2.1): uint32, shaped like field."""
+    _require_cuda(field, "field", torch.float32)
+    lib = _lib.load()
+    nx, ny = dims2_of(field)
+    out = torch.empty(field.shape, dtype=torch.uint32, device=field.device)
+    ws = _ws(lib.dms2_order_workspace_size(nx, ny), field.device)
+    st = status if status is not None else torch.zeros(1, dtype=torch.int32, device=field.device)
+    _check(lib.dms2_order(_ptr(field), nx, ny, _ptr(out), _ptr(ws), ws.numel(), _ptr(st),
+                          _stream(field.device)), "dms2_order")
+    if check and status is None:
+        _device_status_check(st, "dms2_order")
+    return out
+
+
+@dataclass
+class Gradient2d:
+    desc: torch.Tensor  # uint8 [ny, nx]
+    rec: torch.Tensor   # int16 [ny, nx] (bit pattern of the uint16 records)
+
+
+def gradient2d(order_t: torch.Tensor) -> Gradient2d:
+    """ProcessLowerStars on every vertex of a 2D grid (Sec. 2.3)."""
+    _require_cuda(order_t, "order", torch.uint32)
+    lib = _lib.load()
+    nx, ny = dims2_of(order_t)
+    desc = torch.empty(order_t.shape, dtype=torch.uint8, device=order_t.device)
+    rec = torch.empty(order_t.shape, dtype=torch.int16, device=order_t.device)
+    _check(lib.dms2_gradient(_ptr(order_t), nx, ny, _ptr(desc), _ptr(rec),
+                             _stream(order_t.device)), "dms2_gradient")
+    return Gradient2d(desc, rec)
+
+
+def critical2d(g: Gradient2d, caps=None):
+    """Critical vertices, edges and triangles of a 2D gradient, sorted by id.
+    Without caps, a first call sizes the lists (one sync)."""
+    lib = _lib.load()
+    dev = g.desc.device
+    nx, ny = dims2_of(g.desc)
+    ws = _ws(lib.dms2_critical_workspace_size(nx, ny), dev)
+    counts = torch.empty(3, dtype=torch.int64, device=dev)
+
+    def call(cap):
+        lists = [torch.empty(max(int(c), 1), dtype=torch.int64, device=dev) for c in cap]
+        st = torch.zeros(1, dtype=torch.int32, device=dev)
+        cap_arr = (ctypes.c_int64 * 3)(*[int(c) for c in cap])
+        _check(lib.dms2_critical(_ptr(g.desc), _ptr(g.rec), nx, ny, *[_ptr(t) for t in lists],
+                                 cap_arr, _ptr(counts), _ptr(ws), ws.numel(), _ptr(st),
+                                 _stream(dev)), "dms2_critical")
+        return lists, st
+
+    if caps is None:
+        call([0, 0, 0])
+        caps = [int(x) for x in counts.cpu()]
+    lists, st = call(caps)
+    _device_status_check(st, "dms2_critical")
+    n = [int(x) for x in counts.cpu()]
+    return [lists[k][: n[k]] for k in range(3)]
+
+
+@dataclass
+class Diagrams2d:
+    d0: torch.Tensor            # uint8 [n0, 32] pair records (PAIR_DTYPE)
+    d1: torch.Tensor            # uint8 [n1, 32]
+    d0_essential: torch.Tensor  # uint8 [1, 32]
+
+    def numpy(self, which: str) -> np.ndarray:
+        return getattr(self, which).cpu().numpy().view(PAIR_DTYPE).reshape(-1)
+
+
+def diagram_d0d1(field: torch.Tensor, order_t: torch.Tensor, g: Gradient2d, crit) -> Diagrams2d:
+    """D0 and D1 pairs of a 2D field (Alg. 1 and its dual)."""
+    _require_cuda(field, "field", torch.float32)
+    lib = _lib.load()
+    dev = field.device
+    nx, ny = dims2_of(field)
+    nc = [int(c.numel()) for c in crit]
+    ncarr = (ctypes.c_int64 * 3)(*nc)
+    cap0, cap1 = max(nc[0] - 1, 0), nc[2]
+    d0 = torch.empty((max(cap0, 1), PAIR_BYTES), dtype=torch.uint8, device=dev)
+    d1 = torch.empty((max(cap1, 1), PAIR_BYTES), dtype=torch.uint8, device=dev)
+    ess = torch.zeros((1, PAIR_BYTES), dtype=torch.uint8, device=dev)
+    n_out = torch.zeros(2, dtype=torch.int64, device=dev)
+    ws = _ws(lib.dms2_diagram_workspace_size(nx, ny, ncarr), dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    crit_p = [_ptr(c) if c.numel() else None for c in crit]
+    _check(lib.dms2_diagram_d0d1(_ptr(field), _ptr(order_t), _ptr(g.desc), _ptr(g.rec), nx, ny,
+                                 *crit_p, ncarr, _ptr(d0), cap0, _ptr(d1), cap1, _ptr(ess),
+                                 _ptr(n_out), _ptr(ws), ws.numel(), _ptr(st), _stream(dev)),
+           "dms2_diagram_d0d1")
+    _device_status_check(st, "dms2_diagram_d0d1")
+    n = [int(x) for x in n_out.cpu()]
+    return Diagrams2d(d0[: n[0]], d1[: n[1]], ess)
+
+
+@dataclass
+class Result2d:
+    order: torch.Tensor
+    grad: Gradient2d
+    crit: list
+    diagrams: Diagrams2d
+
+
+def diagram2d(field: torch.Tensor) -> Result2d:
+    """The whole path on a 2D field [y, x]: order, gradient, critical
+    simplices, D0 and D1 (the full diagram of a 2D field)."""
+    o = order2d(field)
+    g = gradient2d(o)
+    c = critical2d(g)
+    return Result2d(o, g, c, diagram_d0d1(field, o, g, c))

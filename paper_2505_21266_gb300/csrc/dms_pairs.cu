@@ -748,7 +748,9 @@ struct DiagWs {
   size_t bytes;
 };
 
-DiagWs carve_diag(void* base, const int64_t* nc, int64_t nvert) {
+// nc: counts of the node and saddle lists as for 3D (minima, edges, triangles,
+// tets); nclaim: claim words, one per vertex / tet id the walks may visit
+DiagWs carve_diag(void* base, const int64_t* nc, int64_t nclaim) {
   WsCarver c(base);
   DiagWs w;
   const int64_t nsad = std::max<int64_t>(std::max<int64_t>(nc[1], nc[2]), 1);
@@ -763,7 +765,7 @@ DiagWs carve_diag(void* base, const int64_t* nc, int64_t nvert) {
   w.nd.best = c.take<unsigned long long>(nnode);
   w.nd.age = c.take<uint64_t>(nnode);
   w.nd.immortal = kNone;
-  w.nclaim = 6 * nvert;
+  w.nclaim = nclaim;
   w.claim = c.take<uint32_t>(w.nclaim);
   w.rb = radix64::carve(c, std::max<int64_t>(nsad, 4096));
   w.bytes = c.used;
@@ -824,7 +826,7 @@ int write_diagram(int dim, DiagWs& w, const Dev& D, const float* f, const uint32
 }  // namespace
 
 size_t diagram_workspace_bytes(const Grid& g, const int64_t* n_crit) {
-  return carve_diag(nullptr, n_crit, g.n).bytes;
+  return carve_diag(nullptr, n_crit, 6 * g.n).bytes;
 }
 
 int launch_diagram(const float* f, const uint32_t* order, const uint8_t* desc, const uint64_t* rec,
@@ -832,7 +834,7 @@ int launch_diagram(const float* f, const uint32_t* order, const uint8_t* desc, c
                    const int64_t* crit3, const int64_t* nc, dms_pair* d0, int64_t cap0,
                    dms_pair* d2, int64_t cap2, dms_pair* ess, int64_t* n_out, void* ws,
                    int32_t* dstatus, cudaStream_t s) {
-  DiagWs w = carve_diag(ws, nc, g.n);
+  DiagWs w = carve_diag(ws, nc, 6 * g.n);
   Dev D;
   D.g = g;
   for (int sl = 0; sl < 14; ++sl) {
@@ -1244,7 +1246,7 @@ int diagram_batch_rounds() { return kBatchRounds; }
 // per-field counters and pair-tile sums.
 size_t diagram_batch_workspace_bytes(int64_t nfields, const int64_t* caps, int64_t total) {
   WsCarver c(nullptr);
-  c.take<unsigned char>(carve_diag(nullptr, caps, total).bytes);
+  c.take<unsigned char>(carve_diag(nullptr, caps, 6 * total).bytes);
   const int64_t nsad = std::max<int64_t>(std::max<int64_t>(caps[1], caps[2]), 1);
   const int64_t ntiles = (nsad + PTILE - 1) / PTILE;
   c.take<unsigned long long>(2 * (nfields + 1));
@@ -1260,8 +1262,8 @@ int launch_diagram_batch(const float* f, const uint32_t* order, const uint8_t* d
                          int64_t* pair_offsets, dms_pair* ess, int64_t* pair_totals, void* ws,
                          int32_t* dstatus, cudaStream_t s) {
   WsCarver c(ws);
-  unsigned char* dbase = c.take<unsigned char>(carve_diag(nullptr, caps, total_vertices).bytes);
-  DiagWs w = carve_diag(dbase, caps, total_vertices);
+  unsigned char* dbase = c.take<unsigned char>(carve_diag(nullptr, caps, 6 * total_vertices).bytes);
+  DiagWs w = carve_diag(dbase, caps, 6 * total_vertices);
   const int64_t nsad = std::max<int64_t>(std::max<int64_t>(caps[1], caps[2]), 1);
   const int64_t ntiles = (nsad + PTILE - 1) / PTILE;
   unsigned long long* fcount = c.take<unsigned long long>(2 * (nfields + 1));
@@ -1331,6 +1333,397 @@ int launch_diagram_batch(const float* f, const uint32_t* order, const uint8_t* d
   write(2, w.T2, crit[2], crit[3], cnt_dev + 2, d2, pair_offsets + (nfields + 1), pair_totals + 1,
         fcount + (nfields + 1));
   if (!mem_ok) return DMS_ERR_CUDA;
+  return launch_status();
+}
+
+}  // namespace dms
+
+// ===========================================================================
+// 2D grids: D0 (minima against saddle edges) and D1 (saddle edges against
+// maxima, on the dual graph of triangles plus OUTSIDE) -- the same walks,
+// links and rounds as in 3D, one dimension down.
+//
+// 2D conventions (include/dms.h): vertex v = x + nx*y; edge 3a+k, corner
+// {1,2,3}[k] (+x, +y, +x+y); triangle 2a+k = {a, a+p, a+(1,1)}, p = {+x,
+// +y}[k].  A vertex's six neighbour slots: s < 3 -> +corner, s >= 3 ->
+// -corner of edge type s % 3.  rec2[a] (uint16): bits 3k..3k+2 edge k (0 =
+// absent or paired with its top vertex, 1..2 = paired with the (code-1)-th
+// triangle holding it by increasing id on the unbounded lattice, 7 =
+// critical); bits 9+3k..11+3k triangle k (0 = absent, 1..3 = paired with the
+// facet that omits vertex (code-1) of its chain a < a+p < a+(1,1), 7 =
+// critical).
+// ===========================================================================
+namespace dms {
+namespace {
+
+struct Grid2d {
+  int64_t nx, ny, n;
+};
+
+__device__ __forceinline__ int corner2(int s) { return (s % 3) + 1; }  // {1,2,3}
+__device__ __forceinline__ int64_t cdelta2(const Grid2d& g, int c) {
+  return (c & 1) + ((c >> 1) & 1) * g.nx;
+}
+__device__ __forceinline__ int64_t slot_delta2(const Grid2d& g, int s) {
+  const int64_t d = cdelta2(g, corner2(s));
+  return s < 3 ? d : -d;
+}
+__device__ __forceinline__ void xy2(const Grid2d& g, int64_t v, int64_t& x, int64_t& y) {
+  const uint32_t u = (uint32_t)v, nx = (uint32_t)g.nx;
+  y = u / nx;
+  x = u - (uint32_t)y * nx;
+}
+// the square anchored at (x, y) exists
+__device__ __forceinline__ bool square2(const Grid2d& g, int64_t x, int64_t y) {
+  return x >= 0 && y >= 0 && x + 1 < g.nx && y + 1 < g.ny;
+}
+
+// rank of neighbour order ou among the lower neighbours of vertex t
+__device__ __forceinline__ uint32_t local_rank2d(const Grid2d& g, const uint32_t* __restrict__ order,
+                                                 int64_t t, uint32_t ou) {
+  int64_t x, y;
+  xy2(g, t, x, y);
+  uint32_t r = 0;
+#pragma unroll
+  for (int s = 0; s < 6; ++s) {
+    const int c = corner2(s), sg = s < 3 ? 1 : -1;
+    const int64_t nx = x + sg * (c & 1), ny = y + sg * ((c >> 1) & 1);
+    if (nx < 0 || ny < 0 || nx >= g.nx || ny >= g.ny) continue;
+    r += __ldg(order + t + slot_delta2(g, s)) < ou ? 1u : 0u;
+  }
+  return r;
+}
+
+__global__ void d0_weights2d(Grid2d g, const uint32_t* __restrict__ order,
+                             const int64_t* __restrict__ crit1, int64_t ne, Tri T) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= ne) return;
+  const int64_t id = crit1[i];
+  const int64_t a = id / 3;
+  const int k = (int)(id - a * 3);
+  const int64_t b = a + cdelta2(g, k + 1);
+  const uint32_t oa = __ldg(order + a), ob = __ldg(order + b);
+  const int64_t top = oa > ob ? a : b;
+  T.s[i].w = ((uint64_t)(oa > ob ? oa : ob) << 4) | local_rank2d(g, order, top, oa > ob ? ob : oa);
+  T.s[i].res = kNone;
+}
+
+// D1 saddles are visited by decreasing edge key
+__global__ void d1_weights2d(Grid2d g, const uint32_t* __restrict__ order,
+                             const int64_t* __restrict__ crit1, int64_t ne, Tri T) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= ne) return;
+  const int64_t id = crit1[i];
+  const int64_t a = id / 3;
+  const int k = (int)(id - a * 3);
+  const int64_t b = a + cdelta2(g, k + 1);
+  const uint32_t oa = __ldg(order + a), ob = __ldg(order + b);
+  const int64_t top = oa > ob ? a : b;
+  const uint64_t key =
+      ((uint64_t)(oa > ob ? oa : ob) << 4) | local_rank2d(g, order, top, oa > ob ? ob : oa);
+  T.s[i].w = kMask44 - key;
+  T.s[i].res = kNone;
+}
+
+// node 0 = OUTSIDE (age 0, the oldest); node j + 1 = maximum crit2[j], a
+// higher one older
+__global__ void init_nodes_d1_2d(Grid2d g, const uint32_t* __restrict__ order,
+                                 const int64_t* __restrict__ crit2, int64_t nmax, Nodes nd) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i > nmax) return;
+  nd.parent[i] = (uint32_t)i;
+  nd.best[i] = 0ull;
+  if (i == 0) {
+    nd.age[0] = 0;
+    return;
+  }
+  const int64_t id = crit2[i - 1];
+  const int64_t a = id / 2;
+  const int k = (int)(id - a * 2);
+  const int64_t v[3] = {a, a + cdelta2(g, k + 1), a + cdelta2(g, 3)};
+  uint32_t o[3];
+  int it = 0;
+  for (int j = 0; j < 3; ++j) {
+    o[j] = __ldg(order + v[j]);
+    if (o[j] > o[it]) it = j;
+  }
+  uint32_t r[2];
+  int n = 0;
+  for (int j = 0; j < 3; ++j)
+    if (j != it) r[n++] = local_rank2d(g, order, v[it], o[j]);
+  const uint32_t h = max(r[0], r[1]), l = min(r[0], r[1]);
+  const uint64_t key = ((uint64_t)o[it] << 8) | (h << 4) | l;
+  nd.age[i] = (kMask44 - key) + 1;
+}
+
+// D0 walks: down the vertex-edge pairs (desc) to a minimum
+struct DescWalk2d {
+  Grid2d g;
+  const int64_t* crit1;
+  const uint8_t* desc;
+  uint32_t* claim;
+  struct State {
+    int64_t v, it;
+  };
+  __device__ __forceinline__ bool start(int64_t s, int j, State& st, uint32_t&) const {
+    const int64_t id = crit1[s];
+    const int64_t a = id / 3;
+    const int k = (int)(id - a * 3);
+    st.v = j ? a + cdelta2(g, k + 1) : a;
+    st.it = 0;
+    return true;
+  }
+  __device__ __forceinline__ bool step(State& st, uint32_t w, uint32_t& r,
+                                       int32_t* dstatus) const {
+    const uint8_t d = __ldg(desc + st.v);
+    const uint32_t old = atomicCAS(claim + st.v, kUnclaimed, w);
+    if (old != kUnclaimed) {
+      r = claim_result(old);
+      return false;
+    }
+    if (d >= 6) {  // a minimum without its end mark: inconsistent input
+      set_status(dstatus, DMS_ERR_ARG);
+      r = 0;
+      return false;
+    }
+    st.v += slot_delta2(g, d);
+    if (++st.it > g.n) {
+      set_status(dstatus, DMS_ERR_TIMEOUT);
+      r = 0;
+      return false;
+    }
+    return true;
+  }
+};
+
+// D1 walks: from a triangle through the edge it is paired with to that
+// edge's other triangle, up to a maximum (node j + 1) or out of the grid
+// (OUTSIDE, node 0).  Claims are indexed by triangle id.
+struct DualWalk2d {
+  Grid2d g;
+  const int64_t* crit1;
+  const uint16_t* rec;
+  uint32_t* claim;
+  struct State {
+    int64_t b, bx, by, it;
+    int k;
+  };
+  // triangle j of edge id's two (0 or 1), -1 if that square is outside
+  __device__ __forceinline__ bool start(int64_t s, int j, State& st, uint32_t& r) const {
+    const int64_t id = crit1[s];
+    const int64_t a = id / 3;
+    const int t = (int)(id - a * 3);
+    int64_t ax, ay;
+    xy2(g, a, ax, ay);
+    int64_t bx = ax, by = ay;
+    int k;
+    if (t == 2) {
+      k = j;  // both triangles of the square anchored at a
+    } else if (j == 0) {
+      k = t;  // horizontal: the square above, type 0; vertical: the square to the right, type 1
+    } else {
+      if (t == 0) by -= 1;  // horizontal: the square below, type 1
+      else bx -= 1;         // vertical: the square to the left, type 0
+      k = 1 - t;
+    }
+    if (!square2(g, bx, by)) {
+      r = 0;
+      return false;
+    }
+    st.bx = bx;
+    st.by = by;
+    st.b = bx + g.nx * by;
+    st.k = k;
+    st.it = 0;
+    return true;
+  }
+  __device__ __forceinline__ bool step(State& st, uint32_t w, uint32_t& r,
+                                       int32_t* dstatus) const {
+    const uint32_t rw = __ldg(rec + st.b);
+    const uint32_t old = atomicCAS(claim + st.b * 2 + st.k, kUnclaimed, w);
+    if (old != kUnclaimed) {
+      r = claim_result(old);
+      return false;
+    }
+    const uint32_t code = (rw >> (9 + 3 * st.k)) & 7u;
+    if (code < 1u || code > 3u) {  // a critical triangle without its end mark, or bad data
+      set_status(dstatus, DMS_ERR_ARG);
+      r = 0;
+      return false;
+    }
+    // the paired facet and the triangle across it
+    const int om = (int)code - 1;
+    if (om == 1) {
+      st.k = 1 - st.k;  // the diagonal: the other triangle of the square
+    } else if (st.k == 0) {
+      if (om == 0) {  // vertical edge at b + x: the square to the right
+        st.bx += 1;
+        st.k = 1;
+      } else {  // horizontal edge at b: the square below
+        st.by -= 1;
+        st.k = 1;
+      }
+    } else {
+      if (om == 0) {  // horizontal edge at b + y: the square above
+        st.by += 1;
+        st.k = 0;
+      } else {  // vertical edge at b: the square to the left
+        st.bx -= 1;
+        st.k = 0;
+      }
+    }
+    if (!square2(g, st.bx, st.by)) {
+      r = 0;  // OUTSIDE
+      return false;
+    }
+    st.b = st.bx + g.nx * st.by;
+    if (++st.it > 2 * g.n) {
+      set_status(dstatus, DMS_ERR_TIMEOUT);
+      r = 0;
+      return false;
+    }
+    return true;
+  }
+};
+
+__device__ __forceinline__ int64_t top2(const uint32_t* order, const int64_t* v, int m) {
+  int64_t best = v[0];
+  uint32_t ob = __ldg(order + v[0]);
+  for (int j = 1; j < m; ++j) {
+    const uint32_t o = __ldg(order + v[j]);
+    if (o > ob) {
+      ob = o;
+      best = v[j];
+    }
+  }
+  return best;
+}
+
+// dim 0: (minimum, edge); dim 1: (edge, triangle) -- in saddle-id order
+__global__ void __launch_bounds__(PNT) write_pairs2d(int dim, Grid2d g, const float* __restrict__ f,
+                                                     const uint32_t* __restrict__ order,
+                                                     const int64_t* __restrict__ nodes,
+                                                     const int64_t* __restrict__ crit1, const Tri T,
+                                                     int64_t nsad, const long long* __restrict__ toff,
+                                                     const long long* __restrict__ total,
+                                                     dms_pair* out, int64_t cap, int64_t* n_out,
+                                                     int32_t* dstatus) {
+  __shared__ long long tmp[32];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *n_out = *total;
+    if (*total > cap) set_status(dstatus, DMS_ERR_CAPACITY);
+  }
+  const int64_t base = (int64_t)blockIdx.x * PTILE + (int64_t)threadIdx.x * PITEMS;
+  int c = 0;
+  for (int k = 0; k < PITEMS; ++k) {
+    const int64_t i = base + k;
+    if (i < nsad && T.s[i].res != kNone) ++c;
+  }
+  long long pos = scan64::block_excl(c, tmp, nullptr) + toff[blockIdx.x];
+  for (int k = 0; k < PITEMS; ++k) {
+    const int64_t i = base + k;
+    if (i >= nsad || T.s[i].res == kNone) continue;
+    if (pos < cap) {
+      const int64_t e = crit1[i];
+      const int64_t a = e / 3;
+      const int64_t ev[2] = {a, a + cdelta2(g, (int)(e - a * 3) + 1)};
+      const int64_t et = top2(order, ev, 2);
+      dms_pair p;
+      if (dim == 0) {
+        const int64_t m = nodes[T.s[i].res];
+        p.birth_id = m;
+        p.death_id = e;
+        p.birth = __ldg(f + m);
+        p.death = __ldg(f + et);
+        p.birth_vtx = (uint32_t)m;
+        p.death_vtx = (uint32_t)et;
+      } else {
+        const int64_t tri = nodes[T.s[i].res - 1];  // node 0 (OUTSIDE) never dies
+        const int64_t b = tri / 2;
+        const int64_t tv[3] = {b, b + cdelta2(g, (int)(tri - b * 2) + 1), b + cdelta2(g, 3)};
+        const int64_t tt = top2(order, tv, 3);
+        p.birth_id = e;
+        p.death_id = tri;
+        p.birth = __ldg(f + et);
+        p.death = __ldg(f + tt);
+        p.birth_vtx = (uint32_t)et;
+        p.death_vtx = (uint32_t)tt;
+      }
+      out[pos] = p;
+    }
+    ++pos;
+  }
+}
+
+}  // namespace
+
+size_t diagram2d_workspace_bytes(int64_t n, const int64_t* nc) {
+  const int64_t nc4[4] = {nc[0], nc[1], nc[1], nc[2]};
+  return carve_diag(nullptr, nc4, 2 * n).bytes;
+}
+
+int launch_diagram2d(const float* f, const uint32_t* order, const uint8_t* desc, const uint16_t* rec,
+                     int64_t nx, int64_t ny, const int64_t* crit0, const int64_t* crit1,
+                     const int64_t* crit2, const int64_t* nc, dms_pair* d0, int64_t cap0,
+                     dms_pair* d1, int64_t cap1, dms_pair* ess, int64_t* n_out, void* ws,
+                     int32_t* dstatus, cudaStream_t s) {
+  const Grid2d g{nx, ny, nx * ny};
+  const int64_t nc4[4] = {nc[0], nc[1], nc[1], nc[2]};
+  DiagWs w = carve_diag(ws, nc4, 2 * g.n);
+  const int TB = 256;
+  auto nb = [&](int64_t n) { return (unsigned)std::max<int64_t>(1, (n + TB - 1) / TB); };
+  const int64_t ne = nc[1];
+  auto write = [&](int dim, const int64_t* nodes, dms_pair* out, int64_t cap,
+                   int64_t* nout) -> int {
+    if (ne <= 0)
+      return cudaMemsetAsync(nout, 0, sizeof(int64_t), s) == cudaSuccess ? DMS_OK : DMS_ERR_CUDA;
+    const int64_t ntiles = (ne + PTILE - 1) / PTILE;
+    long long* tc = reinterpret_cast<long long*>(w.rb.ka);
+    long long* sums = reinterpret_cast<long long*>(w.rb.kb);
+    count_pairs<<<(unsigned)ntiles, PNT, 0, s>>>(w.T0, ne, tc); count_launch();
+    scan64::run(tc, ntiles, sums, s);
+    write_pairs2d<<<(unsigned)ntiles, PNT, 0, s>>>(dim, g, f, order, nodes, crit1, w.T0, ne, tc,
+                                                   sums + scan64::num_sums(ntiles), out, cap, nout,
+                                                   dstatus); count_launch();
+    return launch_status();
+  };
+
+  // ---- D0
+  DMS_CUDA_OK(cudaMemsetAsync(w.ctr, 0, 8 * sizeof(unsigned int), s));
+  init_nodes_d0<<<nb(nc[0]), TB, 0, s>>>(order, crit0, nc[0], w.nd); count_launch();
+  write_essential<<<nb(nc[0]), TB, 0, s>>>(f, order, crit0, nc[0], ess); count_launch();
+  if (ne > 0) {
+    DMS_CUDA_OK(cudaMemsetAsync(w.claim, 0xFF, g.n * sizeof(uint32_t), s));
+    mark_ends<<<nb(nc[0]), TB, 0, s>>>(crit0, nullptr, nc[0], 0, w.claim); count_launch();
+    d0_weights2d<<<nb(ne), TB, 0, s>>>(g, order, crit1, ne, w.T0); count_launch();
+    const DescWalk2d wk{g, crit1, desc, w.claim};
+    walk_each<<<nb(ne), TB, 0, s>>>(wk, nullptr, ne, w.T0, dstatus); count_launch();
+    link_walks<<<nb(ne), TB, 0, s>>>(ne, w.T0, w.live0, w.ctr + 0, dstatus); count_launch();
+  }
+  w.nd.immortal = kNone;
+  int st = run_rounds(w, w.T0, s, dstatus);
+  if (st) return st;
+  st = write(0, crit0, d0, cap0, n_out + 0);
+  if (st) return st;
+
+  // ---- D1
+  DMS_CUDA_OK(cudaMemsetAsync(w.ctr, 0, 8 * sizeof(unsigned int), s));
+  init_nodes_d1_2d<<<nb(nc[2] + 1), TB, 0, s>>>(g, order, crit2, nc[2], w.nd); count_launch();
+  if (ne > 0) {
+    DMS_CUDA_OK(cudaMemsetAsync(w.claim, 0xFF, 2 * g.n * sizeof(uint32_t), s));
+    if (nc[2] > 0) {
+      mark_ends<<<nb(nc[2]), TB, 0, s>>>(crit2, nullptr, nc[2], 1, w.claim); count_launch();
+    }
+    d1_weights2d<<<nb(ne), TB, 0, s>>>(g, order, crit1, ne, w.T0); count_launch();
+    const DualWalk2d wk{g, crit1, rec, w.claim};
+    walk_each<<<nb(ne), TB, 0, s>>>(wk, nullptr, ne, w.T0, dstatus); count_launch();
+    link_walks<<<nb(ne), TB, 0, s>>>(ne, w.T0, w.live0, w.ctr + 0, dstatus); count_launch();
+  }
+  w.nd.immortal = 0;  // OUTSIDE
+  st = run_rounds(w, w.T0, s, dstatus);
+  if (st) return st;
+  st = write(1, crit2, d1, cap1, n_out + 1);
+  if (st) return st;
   return launch_status();
 }
 

@@ -50,7 +50,7 @@ def make_field(workload: str, n: int, device, seed=0):
 
 def load_peaks():
     """(HBM GB/s, max SM MHz, which): the measured copy bandwidth and clock of
-    this GPU pool, else the fallback figures."""
+    GPUs, else the fallback figures."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         with open(p) as fh:

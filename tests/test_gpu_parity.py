@@ -14,7 +14,7 @@ import record_decode as rd
 
 pytestmark = pytest.mark.gpu
 
-if not torch.cuda.is_available():  # pragma: no cover - the GPU machine has one
+if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
 import paper_2505_21266_gb300 as dms

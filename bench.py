@@ -49,8 +49,8 @@ def make_field(workload: str, n: int, device, seed=0):
 
 
 def load_peaks():
-    """(HBM GB/s, max SM MHz, which): the measured copy bandwidth and clock of
-    GPUs, else the fallback figures."""
+    """(HBM GB/s, max SM MHz, which): the measured copy bandwidth and SM clock
+    from MEASURED_PEAKS.json, else the fallback figures."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         with open(p) as fh:

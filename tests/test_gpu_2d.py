@@ -129,3 +129,26 @@ def test_2d_errors():
     g = torch.tensor([[0.0, float("nan")], [1.0, 2.0]], device="cuda")
     with pytest.raises(dms.DMSError):
         dms.order2d(g)
+
+
+def test_parity_2d_1024_squared():
+    """The 2D benchmark recipe (64 Gaussians, sigma U[0.01,0.1], + U[0,1e-2))
+    at 1024^2 against the full 2D oracle: order, critical lists, every D0 /
+    D1 pair and its values."""
+    g = np.ascontiguousarray(
+        fields.gaussian_mixture((1, 1024, 1024), 64, (0.01, 0.1), 1e-2, 0).numpy()[0])
+    r = oracle.run2(g)
+    res = dms.diagram2d(torch.from_numpy(g).cuda())
+    torch.cuda.synchronize()
+    assert np.array_equal(res.order.cpu().numpy().reshape(-1), r.order)
+    for d in range(3):
+        assert np.array_equal(res.crit[d].cpu().numpy(), r.crit(d)), d
+    for which, ref, key in (("d0", oracle.D0_2, "death_id"), ("d1", oracle.D1_2, "birth_id")):
+        a = res.diagrams.numpy(which)
+        b = r.get(ref)
+        b = b[np.argsort(b[key], kind="stable")]
+        assert len(a) == len(b)
+        for k in ("birth_id", "death_id", "birth_vtx", "death_vtx"):
+            assert np.array_equal(a[k], b[k]), (which, k)
+        for k in ("birth", "death"):
+            assert np.array_equal(a[k].view(np.uint32), b[k].view(np.uint32)), (which, k)

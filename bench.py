@@ -321,6 +321,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-field batch leg")
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiable leg")
     ap.add_argument("--no-2d", action="store_true", help="skip the 2D leg")
+    ap.add_argument("--leg", choices=["batched", "diff", "2d"], default=None,
+                    help="run one comparison leg alone (its own JSON line), e.g. to profile it")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -339,6 +341,11 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     lib = _lib.load()
+    if args.leg:
+        legs = {"batched": bench_batched, "diff": bench_differentiable, "2d": bench_2d}
+        out = legs[args.leg](dev, args.steps, args.warmup)
+        print(json.dumps({"leg": args.leg, **out}), flush=True)
+        return
 
     wl = WORKLOADS[args.workload]
     n = args.size or wl["n"]

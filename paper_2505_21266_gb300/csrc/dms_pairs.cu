@@ -460,10 +460,13 @@ __global__ void __launch_bounds__(256) walk_each(const W wk, const int64_t* n_de
 
 // Second pass (D0 and D2): resolve both walks of each saddle to their end
 // nodes; a saddle whose walks end at different nodes is live in the pairing.
+// (saddles marked in Sad::pad are left out of the pairing: on 2D grids the
+// D1 pass skips the edges D0 already paired)
 __global__ void link_walks(int64_t nt, Tri T, uint32_t* live, unsigned int* live_n,
-                        int32_t* dstatus) {
+                           int32_t* dstatus, bool skip_marked = false) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= nt) return;
+  if (skip_marked && T.s[i].pad) return;
   const uint32_t n0 = resolve_walk(T.s, T.s[i].ra, 2 * nt, dstatus);
   const uint32_t n1 = resolve_walk(T.s, T.s[i].rb, 2 * nt, dstatus);
   if (n0 == n1) return;
@@ -1406,6 +1409,7 @@ __global__ void d0_weights2d(Grid2d g, const uint32_t* __restrict__ order,
   const int64_t top = oa > ob ? a : b;
   T.s[i].w = ((uint64_t)(oa > ob ? oa : ob) << 4) | local_rank2d(g, order, top, oa > ob ? ob : oa);
   T.s[i].res = kNone;
+  T.s[i].pad = 0;
 }
 
 // D1 saddles are visited by decreasing edge key
@@ -1422,6 +1426,9 @@ __global__ void d1_weights2d(Grid2d g, const uint32_t* __restrict__ order,
   const uint64_t key =
       ((uint64_t)(oa > ob ? oa : ob) << 4) | local_rank2d(g, order, top, oa > ob ? ob : oa);
   T.s[i].w = kMask44 - key;
+  // On a 2D grid (a disk, no 1-cycles survive) every critical edge is either
+  // a D0 death or a D1 birth: the edges D0 paired take no part in D1.
+  T.s[i].pad = T.s[i].res != kNone ? 1u : 0u;
   T.s[i].res = kNone;
 }
 
@@ -1717,7 +1724,7 @@ int launch_diagram2d(const float* f, const uint32_t* order, const uint8_t* desc,
     d1_weights2d<<<nb(ne), TB, 0, s>>>(g, order, crit1, ne, w.T0); count_launch();
     const DualWalk2d wk{g, crit1, rec, w.claim};
     walk_each<<<nb(ne), TB, 0, s>>>(wk, nullptr, ne, w.T0, dstatus); count_launch();
-    link_walks<<<nb(ne), TB, 0, s>>>(ne, w.T0, w.live0, w.ctr + 0, dstatus); count_launch();
+    link_walks<<<nb(ne), TB, 0, s>>>(ne, w.T0, w.live0, w.ctr + 0, dstatus, true); count_launch();
   }
   w.nd.immortal = 0;  // OUTSIDE
   st = run_rounds(w, w.T0, s, dstatus);

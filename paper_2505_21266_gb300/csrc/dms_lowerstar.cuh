@@ -191,11 +191,14 @@ DMS_HD int process_lower_star(uint32_t ox, const uint32_t (&o)[14], const Tables
   uint32_t cE = 0;
   uint64_t cT = 0, C1 = 0, C2 = 0;
   uint32_t cQ = 0, Q1 = 0, Q2 = 0, Q3 = 0;
-  auto classify_edge = [&](int s) {
+  // returns the triangles whose last unclassified edge this was
+  auto classify_edge = [&](int s) -> uint64_t {
     cE |= 1u << s;
     const uint64_t M = tb.edgeCof[s];
+    const uint64_t z = C1 & M & ~C2;
     C2 |= C1 & M;
     C1 |= M;
+    return z;
   };
   auto classify_tri = [&](int j) {
     cT |= 1ull << j;
@@ -209,12 +212,13 @@ DMS_HD int process_lower_star(uint32_t ox, const uint32_t (&o)[14], const Tables
   uint64_t zT = 0;
   uint32_t zQ = 0;
   // PQone: triangles in rank-pair position space (pop-min = find first set),
-  // mirrored in star numbering (pTj) for membership; tets by key scan
-  uint64_t pP0 = 0, pP1 = 0, pTj = 0;
+  // tets by key scan.  PQone holds exactly the unclassified triangles of L
+  // with one classified edge (each is pushed when its first edge is
+  // classified and leaves when it is paired or its second edge is
+  // classified), so membership needs no mask of its own.
+  uint64_t pP0 = 0, pP1 = 0;
   uint32_t pQ = 0;
   auto push_tris = [&](uint64_t nt) {
-    nt &= ~pTj;
-    pTj |= nt;
     for (; nt; nt &= nt - 1) {
       const uint32_t p = tri_pos(ffs64(nt));
       if (p < 64) pP0 |= 1ull << p;
@@ -253,21 +257,27 @@ DMS_HD int process_lower_star(uint32_t ox, const uint32_t (&o)[14], const Tables
         else pP1 &= ~(1ull << (pos - 64));
         const uint32_t hl = tb.hlOfPos[pos];
         const int j = tb.triOfSlots[(INV >> (4 * (hl >> 4))) & 15u][(INV >> (4 * (hl & 15u))) & 15u];
-        pTj &= ~(1ull << j);
-        if ((cT >> j) & 1) continue;
-        if ((C2 >> j) & 1) { zT |= 1ull << j; continue; }  // nuf == 0
         const int beta = ffs32(~cE & (uint32_t)tb.triEdges[j]);
         const int w = beta == tb.triA[j] ? 0 : 1;
         eCode |= (uint64_t)(tb.cofIdx[j][w] + 1) << (4 * beta);
-        classify_edge(beta);
         classify_tri(j);
+        // the other triangles of PQone on beta have no unclassified edge
+        // left: they go to PQzero now rather than when popped.  They are
+        // not the minimum of PQone before then, and PQzero is not popped
+        // while PQone holds anything, so the sequence of pairs is the same.
+        uint64_t z = classify_edge(beta) & TL & ~(1ull << j);
+        zT |= z;
+        for (; z; z &= z - 1) {
+          const uint32_t p = tri_pos(ffs64(z));
+          if (p < 64) pP0 &= ~(1ull << p);
+          else pP1 &= ~(1ull << (p - 64));
+        }
         zE &= ~(1u << beta);
         pQ |= tb.triCof[j] & QL & Q2 & ~Q3 & ~cQ;
-        push_tris(tb.edgeCof[beta] & TL & C1 & ~C2 & ~cT);
+        push_tris(tb.edgeCof[beta] & TL & C1 & ~C2);
       } else {
         const int q = qb;
         pQ &= ~(1u << q);
-        if ((cQ >> q) & 1) continue;
         if ((Q3 >> q) & 1) { zQ |= 1u << q; continue; }  // nuf == 0
         const int beta = ffs64(~cT & tb.tetFmask[q]);
         const int w = beta == tb.tetF[q][0] ? 0 : (beta == tb.tetF[q][1] ? 1 : 2);
@@ -302,7 +312,7 @@ DMS_HD int process_lower_star(uint32_t ox, const uint32_t (&o)[14], const Tables
       zE &= ~(1u << bi);
       eCode |= 7ull << (4 * bi);
       classify_edge(bi);
-      push_tris(tb.edgeCof[bi] & TL & C1 & ~C2 & ~cT);
+      push_tris(tb.edgeCof[bi] & TL & C1 & ~C2);
     } else if (bd == 2) {
       zT &= ~(1ull << bi);
       critT |= 1ull << bi;

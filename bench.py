@@ -60,13 +60,13 @@ def load_peaks():
 
 
 # The gradient kernel is bound by integer instruction issue, not by HBM (it
-# moves 13 B per vertex but executes ~240 warp instructions per vertex).  Its
+# moves 13 B per vertex but executes ~140 warp instructions per vertex).  Its
 # roofline is the issue rate: SMs x 4 schedulers x 32 lanes x SM clock.  The
 # per-vertex figures below are those of the current kernel, from one ncu
-# capture of gradient_kernel on the same field recipe at 384^3 (profiles/
-# gradient_kernel_c3.md): smsp__inst_executed.sum / vertices, and
+# capture of gradient_kernel on the same field recipe at 384^3 (summarised
+# under profiles/): smsp__inst_executed.sum / vertices, and
 # (dram__bytes_read.sum + dram__bytes_write.sum) / vertices.
-GRAD_WARP_INST_PER_VERTEX = 238.38
+GRAD_WARP_INST_PER_VERTEX = 142.64
 GRAD_DRAM_BYTES_PER_VERTEX = 12.30
 GRAD_ALGO_BYTES_PER_VERTEX = 4 + 8 + 1  # read order, write record and desc
 
@@ -458,7 +458,7 @@ def main():
                      "peak_kind": f"derived: {sms} SMs x 4 x 32 lanes x {sm_mhz:.0f} MHz",
                      # the per-vertex figures were measured on the 1024^3 recipe
                      "traffic": GRAD_DRAM_BYTES_PER_VERTEX * nvert if args.workload == "c3" else None,
-                     "figures_from": "gradient_kernel on the c3 recipe (profiles/gradient_kernel_c3.md)",
+                     "figures_from": "ncu capture of gradient_kernel, 384^3 field of the c3 recipe",
                      "kernel_ms": grad_ms, "warp_inst_per_vertex": GRAD_WARP_INST_PER_VERTEX,
                      "hbm": {"algorithmic_bytes": grad_bytes,
                              "achieved_gbs": grad_bytes / (grad_ms / 1e3) / 1e9,

@@ -59,6 +59,7 @@ struct Smem {
   lowerstar::Keys<NT> keys;
   uint16_t perm[(TX + 1) * (TY + 1)];  // slab vertices grouped by lower-star size
   uint8_t kcnt[(TX + 1) * (TY + 1)];
+  uint16_t lmask[(TX + 1) * (TY + 1)];
   unsigned int bucket[64];
   unsigned int next_task;
   unsigned int counts[4];
@@ -117,25 +118,19 @@ __device__ void gradient_tile(Smem<TY>& sm, const uint32_t* __restrict__ order, 
     __syncthreads();
     for (int i = tid; i < nvx * nvy; i += NT) {
       const int lx = i % nvx, ly = i / nvx;
-      uint32_t k = 0;
+      uint32_t k = 0, lm = 0;
       if (x0 + lx < g.nx && y0 + ly < g.ny) {
         const uint32_t ox = w0[ly + 1][lx + 1];
-        uint64_t notT = 0;
-        uint32_t notQ = 0;
         static_for<0, 14>([&](auto S) {
           constexpr int s = decltype(S)::value;
           constexpr int dx = kStar.off[s][0], dy = kStar.off[s][1], dz = kStar.off[s][2];
-          constexpr uint64_t ts = kStar.edgeCof[s];
-          constexpr uint32_t qs = lowerstar::kSlotTets[s];
           const Row* w = dz < 0 ? wm : (dz > 0 ? wp : w0);
-          if (!(w[ly + 1 + dy][lx + 1 + dx] < ox)) {
-            notT |= ts;
-            notQ |= qs;
-          }
+          lm |= (w[ly + 1 + dy][lx + 1 + dx] < ox ? 1u : 0u) << s;
         });
-        k = (uint32_t)(__popcll(((1ull << 36) - 1) & ~notT) + __popc(((1u << 24) - 1) & ~notQ));
+        k = (uint32_t)(__popcll(lowerstar::lower_tris(sm.tb, lm)) + __popc(lowerstar::lower_tets(sm.tb, lm)));
       }
       sm.kcnt[i] = (uint8_t)k;
+      sm.lmask[i] = (uint16_t)lm;
       atomicAdd(&sm.bucket[k], 1u);
     }
     __syncthreads();
@@ -165,9 +160,8 @@ __device__ void gradient_tile(Smem<TY>& sm, const uint32_t* __restrict__ order, 
           const Row* w = dz < 0 ? wm : (dz > 0 ? wp : w0);
           o[s] = w[cy + dy][cx + dx];
         });
-        const uint32_t ox = w0[cy][cx];
         uint64_t acc[8];
-        int d = lowerstar::process_lower_star<NT>(ox, o, sm.tb, sm.keys, tid, acc);
+        int d = lowerstar::process_lower_star<NT>(sm.lmask[idx], o, sm.tb, sm.keys, tid, acc);
         const bool owned = lx < TX && ly < TY && z < zend;
         if (owned) {
           desc[x + g.nx * (y + g.ny * z)] = (uint8_t)d;

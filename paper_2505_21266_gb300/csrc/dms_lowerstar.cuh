@@ -87,7 +87,19 @@ struct Tables {
   uint8_t triOfSlots[14][14];  // star triangle on slots (a, b), 255 if none
   uint8_t hlOfPos[91];         // rank-pair position -> (h << 4) | l
   uint8_t pad[1];
+  // star triangles / tets with a slot outside m, for the low (0..6) and
+  // high (7..13) seven bits m of the mask of lower slots
+  uint64_t notTlo[128], notThi[128];
+  uint32_t notQlo[128], notQhi[128];
+  uint64_t bit[64];              // 1 << i
+  uint64_t posLo[91], posHi[91];  // position p as a bit of (pP0, pP1)
 };
+DMS_HD uint64_t lower_tris(const Tables& tb, uint32_t lm) {
+  return ~(tb.notTlo[lm & 127u] | tb.notThi[lm >> 7]) & ((1ull << 36) - 1);
+}
+DMS_HD uint32_t lower_tets(const Tables& tb, uint32_t lm) {
+  return ~(tb.notQlo[lm & 127u] | tb.notQhi[lm >> 7]) & ((1u << 24) - 1);
+}
 
 // per-thread precomputed keys, stored transposed ([item][thread]) so that a
 // warp touches consecutive bytes: triangle rank-pair positions and 12-bit tet
@@ -99,8 +111,10 @@ struct Keys {
 };
 
 // ProcessLowerStars for one vertex.  o[s] = order of neighbour s
-// (0xFFFFFFFF outside the grid), ox = order of x.  Returns desc and fills
-// acc[c], the record bits contributed to the anchor x - corner c.
+// (0xFFFFFFFF outside the grid), lm = the mask of the slots s with
+// o[s] < order of x (the caller has it from its load-balancing pass).
+// Returns desc and fills acc[c], the record bits contributed to the anchor
+// x - corner c.
 //
 // Keys.  Every simplex of L(x) holds x, its top vertex, so the lexicographic
 // comparison of Sec. 2.1 reduces to the ranks (among the lower neighbours of
@@ -109,13 +123,10 @@ struct Keys {
 // Triangles are also numbered by their rank pair, position h*(h-1)/2 + l,
 // in which increasing positions are increasing keys.
 template <int NT>
-DMS_HD int process_lower_star(uint32_t ox, const uint32_t (&o)[14], const Tables& tb,
+DMS_HD int process_lower_star(uint32_t lm, const uint32_t (&o)[14], const Tables& tb,
                               Keys<NT>& keys, int tid, uint64_t (&acc)[8]) {
 #pragma unroll
   for (int c = 0; c < 8; ++c) acc[c] = 0;
-  uint32_t lm = 0;
-#pragma unroll
-  for (int s = 0; s < 14; ++s) lm |= (o[s] < ox ? 1u : 0u) << s;
   if (lm == 0) return 15;  // no lower edge: a minimum
 
   // ranks among the lower neighbours: one comparison per pair of slots
@@ -138,39 +149,22 @@ DMS_HD int process_lower_star(uint32_t ox, const uint32_t (&o)[14], const Tables
   auto rank = [&](int s) -> uint32_t { return (uint32_t)(R >> (4 * s)) & 15u; };
 
   // the lower star: every star simplex without a non-lower slot
-  uint64_t notT = 0;
-  uint32_t notQ = 0;
-  static_for<0, 14>([&](auto S) {
-    constexpr int s = decltype(S)::value;
-    constexpr uint64_t ts = kStar.edgeCof[s];
-    constexpr uint32_t qs = kSlotTets[s];
-    if (!((lm >> s) & 1)) {
-      notT |= ts;
-      notQ |= qs;
-    }
-  });
-  const uint64_t TL = ((1ull << 36) - 1) & ~notT;
-  const uint32_t QL = ((1u << 24) - 1) & ~notQ;
+  const uint64_t TL = lower_tris(tb, lm);
+  const uint32_t QL = lower_tets(tb, lm);
 
-  static_for<0, 36>([&](auto J) {
-    constexpr int j = decltype(J)::value;
-    constexpr int a = kStar.triA[j], b = kStar.triB[j];
-    if ((TL >> j) & 1) {
-      const uint32_t ra = rank(a), rb = rank(b);
-      const uint32_t h = umax(ra, rb), l = umin(ra, rb);
-      keys.tp[j][tid] = (uint8_t)((h * (h - 1)) / 2 + l);
-    }
-  });
-  static_for<0, 24>([&](auto Q) {
-    constexpr int q = decltype(Q)::value;
-    constexpr int a = kStar.tetA[q], b = kStar.tetB[q], c = kStar.tetC[q];
-    if ((QL >> q) & 1) {
-      const uint32_t ra = rank(a), rb = rank(b), rc = rank(c);
-      const uint32_t h = umax(ra, umax(rb, rc)), l = umin(ra, umin(rb, rc));
-      const uint32_t m = ra + rb + rc - h - l;
-      keys.q[q][tid] = (uint16_t)(((h + 1) << 8) | ((m + 1) << 4) | (l + 1));
-    }
-  });
+  for (uint64_t mt = TL; mt; mt &= mt - 1) {
+    const int j = ffs64(mt);
+    const uint32_t ra = rank(tb.triA[j]), rb = rank(tb.triB[j]);
+    const uint32_t h = umax(ra, rb), l = umin(ra, rb);
+    keys.tp[j][tid] = (uint8_t)((h * (h - 1)) / 2 + l);
+  }
+  for (uint32_t mq = QL; mq; mq &= mq - 1) {
+    const int q = ffs32(mq);
+    const uint32_t ra = rank(tb.tetS[q][0]), rb = rank(tb.tetS[q][1]), rc = rank(tb.tetS[q][2]);
+    const uint32_t h = umax(ra, umax(rb, rc)), l = umin(ra, umin(rb, rc));
+    const uint32_t m = ra + rb + rc - h - l;
+    keys.q[q][tid] = (uint16_t)(((h + 1) << 8) | ((m + 1) << 4) | (l + 1));
+  }
   auto tri_pos = [&](int j) -> uint32_t { return keys.tp[j][tid]; };
   auto pos_key = [&](uint32_t p) -> uint32_t {
     const uint32_t hl = tb.hlOfPos[p];
@@ -184,10 +178,10 @@ DMS_HD int process_lower_star(uint32_t ox, const uint32_t (&o)[14], const Tables
   // nuf is tracked bit-parallel: C1/C2 = triangles with >= 1 / 2 classified
   // edges, Q1/Q2/Q3 = tets with >= 1 / 2 / 3 classified facet triangles, so
   // "nuf == 1" is C1 & ~C2 (triangles) or Q2 & ~Q3 (tets) and every push of
-  // cofacets is a handful of mask operations.  The two nested loops of the
-  // algorithm (drain PQone, then pop one PQzero element) are one flat loop
-  // whose body pops from PQone when it is non-empty and from PQzero
-  // otherwise -- the same sequence of pops, with less divergence.
+  // cofacets is a handful of mask operations.  PQone is drained in two
+  // uniform loops (triangles, then tets; see below) rather than by one pop
+  // loop that branches on the type of the minimum, which keeps the lanes of
+  // a warp on the same path.
   uint32_t cE = 0;
   uint64_t cT = 0, C1 = 0, C2 = 0;
   uint32_t cQ = 0, Q1 = 0, Q2 = 0, Q3 = 0;
@@ -201,7 +195,7 @@ DMS_HD int process_lower_star(uint32_t ox, const uint32_t (&o)[14], const Tables
     return z;
   };
   auto classify_tri = [&](int j) {
-    cT |= 1ull << j;
+    cT |= tb.bit[j];
     const uint32_t M = tb.triCof[j];
     Q3 |= Q2 & M;
     Q2 |= Q1 & M;
@@ -221,8 +215,8 @@ DMS_HD int process_lower_star(uint32_t ox, const uint32_t (&o)[14], const Tables
   auto push_tris = [&](uint64_t nt) {
     for (; nt; nt &= nt - 1) {
       const uint32_t p = tri_pos(ffs64(nt));
-      if (p < 64) pP0 |= 1ull << p;
-      else pP1 |= 1ull << (p - 64);
+      pP0 |= tb.posLo[p];
+      pP1 |= tb.posHi[p];
     }
   };
   push_tris(tb.edgeCof[delta] & TL);  // their other edge is unclassified
@@ -238,56 +232,53 @@ DMS_HD int process_lower_star(uint32_t ox, const uint32_t (&o)[14], const Tables
   };
 
   for (;;) {
-    if (pP0 | pP1 | pQ) {
-      uint32_t bestT = 0xFFFFu;
-      int pos = 0;
-      if (pP0 | pP1) {
-        pos = pP0 ? ffs64(pP0) : 64 + ffs64(pP1);
-        bestT = pos_key(pos);
+    // Drain PQone: its triangles first, then its tets.  A tet pop changes
+    // nothing a triangle pop reads (it classifies a triangle already in
+    // PQzero), every facet of a tet has a smaller key than the tet, and tets
+    // pushed by a triangle have larger keys than it, so this visits the
+    // same pairs as popping triangles and tets by one key order.
+    while (pP0 | pP1) {
+      const int pos = pP0 ? ffs64(pP0) : 64 + ffs64(pP1);
+      pP0 &= ~tb.posLo[pos];
+      pP1 &= ~tb.posHi[pos];
+      const uint32_t hl = tb.hlOfPos[pos];
+      const int j = tb.triOfSlots[(INV >> (4 * (hl >> 4))) & 15u][(INV >> (4 * (hl & 15u))) & 15u];
+      const int beta = ffs32(~cE & (uint32_t)tb.triEdges[j]);
+      const int w = beta == tb.triA[j] ? 0 : 1;
+      eCode |= (uint64_t)(tb.cofIdx[j][w] + 1) << (4 * beta);
+      classify_tri(j);
+      // the other triangles of PQone on beta have no unclassified edge
+      // left: they go to PQzero now rather than when popped.  They are
+      // not the minimum of PQone before then, and PQzero is not popped
+      // while PQone holds anything, so the sequence of pairs is the same.
+      uint64_t z = classify_edge(beta) & TL & ~tb.bit[j];
+      zT |= z;
+      for (; z; z &= z - 1) {
+        const uint32_t p = tri_pos(ffs64(z));
+        pP0 &= ~tb.posLo[p];
+        pP1 &= ~tb.posHi[p];
       }
+      zE &= ~(1u << beta);
+      pQ |= tb.triCof[j] & QL & Q2 & ~Q3 & ~cQ;
+      push_tris(tb.edgeCof[beta] & TL & C1 & ~C2);
+    }
+    while (pQ) {
       uint32_t bestQ = 0xFFFFu;
-      int qb = 0;
+      int q = 0;
       for (uint32_t m = pQ; m; m &= m - 1) {
-        int q = ffs32(m);
-        uint32_t k = tet_key(q);
-        if (k < bestQ) { bestQ = k; qb = q; }
+        const int qq = ffs32(m);
+        const uint32_t k = tet_key(qq);
+        if (k < bestQ) { bestQ = k; q = qq; }
       }
-      if (bestT < bestQ) {
-        if (pos < 64) pP0 &= ~(1ull << pos);
-        else pP1 &= ~(1ull << (pos - 64));
-        const uint32_t hl = tb.hlOfPos[pos];
-        const int j = tb.triOfSlots[(INV >> (4 * (hl >> 4))) & 15u][(INV >> (4 * (hl & 15u))) & 15u];
-        const int beta = ffs32(~cE & (uint32_t)tb.triEdges[j]);
-        const int w = beta == tb.triA[j] ? 0 : 1;
-        eCode |= (uint64_t)(tb.cofIdx[j][w] + 1) << (4 * beta);
-        classify_tri(j);
-        // the other triangles of PQone on beta have no unclassified edge
-        // left: they go to PQzero now rather than when popped.  They are
-        // not the minimum of PQone before then, and PQzero is not popped
-        // while PQone holds anything, so the sequence of pairs is the same.
-        uint64_t z = classify_edge(beta) & TL & ~(1ull << j);
-        zT |= z;
-        for (; z; z &= z - 1) {
-          const uint32_t p = tri_pos(ffs64(z));
-          if (p < 64) pP0 &= ~(1ull << p);
-          else pP1 &= ~(1ull << (p - 64));
-        }
-        zE &= ~(1u << beta);
-        pQ |= tb.triCof[j] & QL & Q2 & ~Q3 & ~cQ;
-        push_tris(tb.edgeCof[beta] & TL & C1 & ~C2);
-      } else {
-        const int q = qb;
-        pQ &= ~(1u << q);
-        if ((Q3 >> q) & 1) { zQ |= 1u << q; continue; }  // nuf == 0
-        const int beta = ffs64(~cT & tb.tetFmask[q]);
-        const int w = beta == tb.tetF[q][0] ? 0 : (beta == tb.tetF[q][1] ? 1 : 2);
-        set_tet_code(q, tb.tetCode[q][w]);
-        classify_tri(beta);
-        cQ |= 1u << q;
-        zT &= ~(1ull << beta);
-        pQ |= tb.triCof[beta] & QL & Q2 & ~Q3 & ~cQ;
-      }
-      continue;
+      pQ &= ~(1u << q);
+      if ((Q3 >> q) & 1) { zQ |= 1u << q; continue; }  // nuf == 0
+      const int beta = ffs64(~cT & tb.tetFmask[q]);
+      const int w = beta == tb.tetF[q][0] ? 0 : (beta == tb.tetF[q][1] ? 1 : 2);
+      set_tet_code(q, tb.tetCode[q][w]);
+      classify_tri(beta);
+      cQ |= 1u << q;
+      zT &= ~tb.bit[beta];
+      pQ |= tb.triCof[beta] & QL & Q2 & ~Q3 & ~cQ;
     }
     if (!(zE | zT | zQ)) break;
     // pop-min of PQzero: the next critical simplex
@@ -379,6 +370,23 @@ constexpr Tables make_tables() {
   }
   for (int h = 1; h < 14; ++h)
     for (int l = 0; l < h; ++l) t.hlOfPos[h * (h - 1) / 2 + l] = (uint8_t)((h << 4) | l);
+  for (int i = 0; i < 64; ++i) t.bit[i] = 1ull << i;
+  for (int p = 0; p < 91; ++p) {
+    t.posLo[p] = p < 64 ? 1ull << p : 0;
+    t.posHi[p] = p < 64 ? 0 : 1ull << (p - 64);
+  }
+  for (int m = 0; m < 128; ++m) {
+    t.notTlo[m] = t.notThi[m] = 0;
+    t.notQlo[m] = t.notQhi[m] = 0;
+    for (int s = 0; s < 7; ++s) {
+      if (!((m >> s) & 1)) {
+        t.notTlo[m] |= kStar.edgeCof[s];
+        t.notQlo[m] |= kSlotTets[s];
+        t.notThi[m] |= kStar.edgeCof[s + 7];
+        t.notQhi[m] |= kSlotTets[s + 7];
+      }
+    }
+  }
   return t;
 }
 

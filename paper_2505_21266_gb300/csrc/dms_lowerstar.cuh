@@ -92,6 +92,7 @@ struct Tables {
   uint64_t notTlo[128], notThi[128];
   uint32_t notQlo[128], notQhi[128];
   uint64_t bit[64];              // 1 << i
+  uint64_t nib[16];              // 1 << 4i
   uint64_t posLo[91], posHi[91];  // position p as a bit of (pP0, pP1)
 };
 DMS_HD uint64_t lower_tris(const Tables& tb, uint32_t lm) {
@@ -227,7 +228,7 @@ DMS_HD int process_lower_star(uint32_t lm, const uint32_t (&o)[14], const Tables
   uint32_t qCode1 = 0;
   uint64_t critT = 0;
   auto set_tet_code = [&](int q, uint32_t code) {
-    if (q < 16) qCode0 |= (uint64_t)code << (4 * q);
+    if (q < 16) qCode0 |= (uint64_t)code * tb.nib[q];
     else qCode1 |= code << (4 * (q - 16));
   };
 
@@ -245,7 +246,7 @@ DMS_HD int process_lower_star(uint32_t lm, const uint32_t (&o)[14], const Tables
       const int j = tb.triOfSlots[(INV >> (4 * (hl >> 4))) & 15u][(INV >> (4 * (hl & 15u))) & 15u];
       const int beta = ffs32(~cE & (uint32_t)tb.triEdges[j]);
       const int w = beta == tb.triA[j] ? 0 : 1;
-      eCode |= (uint64_t)(tb.cofIdx[j][w] + 1) << (4 * beta);
+      eCode |= (uint64_t)(tb.cofIdx[j][w] + 1) * tb.nib[beta];
       classify_tri(j);
       // the other triangles of PQone on beta have no unclassified edge
       // left: they go to PQzero now rather than when popped.  They are
@@ -371,6 +372,7 @@ constexpr Tables make_tables() {
   for (int h = 1; h < 14; ++h)
     for (int l = 0; l < h; ++l) t.hlOfPos[h * (h - 1) / 2 + l] = (uint8_t)((h << 4) | l);
   for (int i = 0; i < 64; ++i) t.bit[i] = 1ull << i;
+  for (int i = 0; i < 16; ++i) t.nib[i] = 1ull << (4 * i);
   for (int p = 0; p < 91; ++p) {
     t.posLo[p] = p < 64 ? 1ull << p : 0;
     t.posHi[p] = p < 64 ? 0 : 1ull << (p - 64);

@@ -22,11 +22,13 @@
 //
 // Load balance.  The work of a vertex grows with the size of its lower star
 // and the lanes of a warp run in lock-step, so before processing a slab the
-// CTA counts, for each of its vertices, the simplices of the lower star
-// (from the mask of lower neighbours), buckets the vertices by that count
-// and hands them to warps in groups of 32, largest lower stars first, each
-// warp taking the next group when it is done (longest-first list
-// scheduling).  On i.i.d. noise this halves the kernel time.
+// CTA sizes, for each of its vertices, the two loops of ProcessLowerStars
+// (from the mask of lower neighbours: the number of lower neighbours, which
+// bounds the triangle pops, and of lower-star tets, the tet pops), buckets
+// the vertices by that pair and hands them to warps in groups of 32,
+// largest first, each warp taking the next group when it is done
+// (longest-first list scheduling).  On i.i.d. noise this halves the kernel
+// time.
 #include <algorithm>
 #include <cstdint>
 #include <type_traits>
@@ -58,9 +60,9 @@ struct Smem {
   unsigned long long recs[2][TY][TX];
   lowerstar::Keys<NT> keys;
   uint16_t perm[(TX + 1) * (TY + 1)];  // slab vertices grouped by lower-star size
-  uint8_t kcnt[(TX + 1) * (TY + 1)];
+  uint8_t kcnt[(TX + 1) * (TY + 1)];   // bucket: 16 x lower neighbours + lower tets (<= 15)
   uint16_t lmask[(TX + 1) * (TY + 1)];
-  unsigned int bucket[64];
+  unsigned int bucket[256];
   unsigned int next_task;
   unsigned int counts[4];
   long long tile;  // batched kernel: the tile this CTA works on
@@ -114,7 +116,7 @@ __device__ void gradient_tile(Smem<TY>& sm, const uint32_t* __restrict__ order, 
     const Row* wp = sm.win[(z + 1) % 3];
     // group the slab's vertices by the size of their lower star so that the
     // lanes of a warp get similar work; warps take groups largest-first
-    if (tid < 64) sm.bucket[tid] = 0;
+    for (int b = tid; b < 256; b += NT) sm.bucket[b] = 0;
     __syncthreads();
     for (int i = tid; i < nvx * nvy; i += NT) {
       const int lx = i % nvx, ly = i / nvx;
@@ -127,21 +129,31 @@ __device__ void gradient_tile(Smem<TY>& sm, const uint32_t* __restrict__ order, 
           const Row* w = dz < 0 ? wm : (dz > 0 ? wp : w0);
           lm |= (w[ly + 1 + dy][lx + 1 + dx] < ox ? 1u : 0u) << s;
         });
-        k = (uint32_t)(__popcll(lowerstar::lower_tris(sm.tb, lm)) + __popc(lowerstar::lower_tets(sm.tb, lm)));
+        const uint32_t kl = __popc(lm), nq = __popc(lowerstar::lower_tets(sm.tb, lm));
+        k = kl * 16u + min(nq, 15u);  // < 15 * 16
       }
       sm.kcnt[i] = (uint8_t)k;
       sm.lmask[i] = (uint16_t)lm;
       atomicAdd(&sm.bucket[k], 1u);
     }
     __syncthreads();
-    if (tid == 0) {
-      unsigned int acc = 0;
-      sm.next_task = NT / 32;  // the first task of each warp is its own index
-      for (int k = 63; k >= 0; --k) {  // largest lower stars first
-        const unsigned int c = sm.bucket[k];
-        sm.bucket[k] = acc;
-        acc += c;
+    if (warp == 0) {  // exclusive offsets, largest keys first
+      constexpr int C = 256 / 32;
+      unsigned int cs = 0;
+      for (int c = 0; c < C; ++c) cs += sm.bucket[256 - 1 - (lane * C + c)];
+      unsigned int inc = cs;
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        if (lane >= o) inc += y;
       }
+      unsigned int acc = inc - cs;
+      for (int c = 0; c < C; ++c) {
+        const int b = 256 - 1 - (lane * C + c);
+        const unsigned int cnt = sm.bucket[b];
+        sm.bucket[b] = acc;
+        acc += cnt;
+      }
+      if (lane == 0) sm.next_task = NT / 32;  // the first task of each warp is its own index
     }
     __syncthreads();
     for (int i = tid; i < nvx * nvy; i += NT) sm.perm[atomicAdd(&sm.bucket[sm.kcnt[i]], 1u)] = (uint16_t)i;

@@ -66,8 +66,8 @@ def load_peaks():
 # capture of gradient_kernel on the same field recipe at 384^3 (summarised
 # under profiles/): smsp__inst_executed.sum / vertices, and
 # (dram__bytes_read.sum + dram__bytes_write.sum) / vertices.
-GRAD_WARP_INST_PER_VERTEX = 142.64
-GRAD_DRAM_BYTES_PER_VERTEX = 12.30
+GRAD_WARP_INST_PER_VERTEX = 140.43
+GRAD_DRAM_BYTES_PER_VERTEX = 12.27
 GRAD_ALGO_BYTES_PER_VERTEX = 4 + 8 + 1  # read order, write record and desc
 
 

@@ -143,6 +143,45 @@ __device__ __forceinline__ int tet_type(int c1, int c2) {
   return (c1 >> 1) * 2 + ((c2 ^ c1) > (7 ^ c2) ? 1 : 0);
 }
 
+// One step of an ascending dual path, tabulated.  Tet type k (chain
+// 0 < c1 < c2 < 7 of its anchor cube) paired with the facet that omits
+// chain vertex code - 1 leaves through that facet into the other tet on it:
+//  * code 1 omits the anchor: the next tet is anchored at anchor + c1, chain
+//    (c2 ^ c1, 7 ^ c1);
+//  * code 4 omits the top: anchored at anchor - (7 ^ c2), chain
+//    (7 ^ c2, (7 ^ c2) | c1);
+//  * code 2 / 3 omit c1 / c2: same anchor, chain (c2 ^ c1, c2) / (c1, c1 | (7 ^ c2)).
+// Entry 4k + code - 1 is a byte: next type (bits 0-2), anchor step corner
+// (3-5), step sign (6-7: 0 none, 1 plus, 2 minus); 24 entries in three
+// 64-bit immediates.
+namespace dual_step_detail {
+constexpr int c1_of(int k) { return (0x442211 >> (4 * k)) & 15; }
+constexpr int c2_of(int k) { return (0x656353 >> (4 * k)) & 15; }
+constexpr int type_of(int c1, int c2) { return (c1 >> 1) * 2 + ((c2 ^ c1) > (7 ^ c2) ? 1 : 0); }
+constexpr uint64_t entry(int e) {
+  const int k = e / 4, code = e % 4 + 1, c1 = c1_of(k), c2 = c2_of(k);
+  int stp = 0, sg = 0, n1 = 0, n2 = 0;
+  if (code == 1) { stp = c1; sg = 1; n1 = c2 ^ c1; n2 = 7 ^ c1; }
+  else if (code == 4) { stp = 7 ^ c2; sg = 2; n1 = stp; n2 = stp | c1; }
+  else if (code == 2) { n1 = c2 ^ c1; n2 = c2; }
+  else { n1 = c1; n2 = c1 | (7 ^ c2); }
+  return (uint64_t)(type_of(n1, n2) | (stp << 3) | (sg << 6));
+}
+constexpr uint64_t word(int w) {
+  uint64_t x = 0;
+  for (int i = 0; i < 8; ++i) x |= entry(8 * w + i) << (8 * i);
+  return x;
+}
+}  // namespace dual_step_detail
+constexpr uint64_t kDualStep0 = dual_step_detail::word(0);
+constexpr uint64_t kDualStep1 = dual_step_detail::word(1);
+constexpr uint64_t kDualStep2 = dual_step_detail::word(2);
+__device__ __forceinline__ uint32_t dual_step(int k, uint32_t code) {
+  const uint32_t e = 4 * k + code - 1;
+  const uint64_t w = e < 8 ? kDualStep0 : (e < 16 ? kDualStep1 : kDualStep2);
+  return (uint32_t)(w >> (8 * (e & 7))) & 255u;
+}
+
 // Walks with path sharing: every vertex (D0) or non-critical tet (D2) a walk
 // passes is claimed for it (atomicCAS on claim[id]); a walk that reaches an id
 // claimed by another walk stops there, since from there on both follow the
@@ -408,25 +447,20 @@ struct DualWalk {
       r = 0;
       return false;
     }
-    const int c1 = tet_c1(st.k), c2 = tet_c2(st.k);
-    int n1, n2, stp = 0, sg = 0;
-    switch (code - 1) {
-      case 0: stp = c1; sg = 1; n1 = c2 ^ c1; n2 = 7 ^ c1; break;    // omits the anchor
-      case 3: stp = 7 ^ c2; sg = -1; n1 = stp; n2 = stp | c1; break;  // omits the top
-      case 1: n1 = c2 ^ c1; n2 = c2; break;
-      default: n1 = c1; n2 = c1 | (7 ^ c2); break;
+    // the next tet, without branching on the code (lanes take different
+    // codes): a zero step leaves the anchor where it is
+    const uint32_t t = dual_step(st.k, code);
+    const int stp = (int)((t >> 3) & 7u);
+    const int sg = (t >> 6) == 1u ? 1 : ((t >> 6) == 2u ? -1 : 0);
+    st.bx += sg * (stp & 1);
+    st.by += sg * ((stp >> 1) & 1);
+    st.bz += sg * ((stp >> 2) & 1);
+    if (!fits(st.g, st.bx, st.by, st.bz, 7)) {
+      r = 0;  // left the grid: OUTSIDE
+      return false;
     }
-    if (sg) {
-      st.bx += sg * (stp & 1);
-      st.by += sg * ((stp >> 1) & 1);
-      st.bz += sg * ((stp >> 2) & 1);
-      if (!fits(st.g, st.bx, st.by, st.bz, 7)) {
-        r = 0;  // left the grid: OUTSIDE
-        return false;
-      }
-      st.b += sg * corner_delta(st.g, stp);
-    }
-    st.k = tet_type(n1, n2);
+    st.b += sg * corner_delta(st.g, stp);
+    st.k = (int)(t & 7u);
     if (++st.it > 6 * st.g.n) {
       set_status(dstatus, DMS_ERR_TIMEOUT);
       r = 0;

@@ -62,6 +62,16 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
 
+def _to_host(t: torch.Tensor) -> torch.Tensor:
+    """A host copy of t; device tensors land in page-locked memory (the copy
+    runs at the link's rate, and torch's host allocator reuses the buffers)."""
+    if not t.is_cuda:
+        return t
+    h = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+    h.copy_(t)
+    return h
+
+
 def _ws(nbytes: int, device) -> torch.Tensor:
     return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
 
@@ -139,8 +149,7 @@ class Diagrams:
     d0_essential: torch.Tensor  # uint8 [1, 32]
 
     def numpy(self, which: str) -> np.ndarray:
-        t = getattr(self, which)
-        return t.cpu().numpy().view(PAIR_DTYPE).reshape(-1)
+        return _to_host(getattr(self, which)).numpy().view(PAIR_DTYPE).reshape(-1)
 
 
 def diagram_d0d2(field: torch.Tensor, order_t: torch.Tensor, g: Gradient, crit,
@@ -337,7 +346,7 @@ class Diagrams2d:
     d0_essential: torch.Tensor  # uint8 [1, 32]
 
     def numpy(self, which: str) -> np.ndarray:
-        return getattr(self, which).cpu().numpy().view(PAIR_DTYPE).reshape(-1)
+        return _to_host(getattr(self, which)).numpy().view(PAIR_DTYPE).reshape(-1)
 
 
 def diagram_d0d1(field: torch.Tensor, order_t: torch.Tensor, g: Gradient2d, crit) -> Diagrams2d:

@@ -408,8 +408,10 @@ def main():
     t_end = torch.cuda.Event(enable_timing=True)
     gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
+    sev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     t_start.record(stream)
     for k in range(args.steps):
+        sev[k].record(stream)
         step(f, gev[k])
     t_end.record(stream)
     torch.cuda.synchronize()
@@ -417,6 +419,13 @@ def main():
     clocks = sampler.stop()
     ms = t_start.elapsed_time(t_end)
     grad_ms = statistics.mean(a.elapsed_time(b) for a, b in gev)
+    # per-stage times of the timed steps (events between the stages, no
+    # synchronisation): order, gradient, and critical + D0/D2 to the next step
+    ends = sev[1:] + [t_end]
+    stages = {"order": statistics.mean(sev[k].elapsed_time(gev[k][0]) for k in range(args.steps)),
+              "gradient": grad_ms,
+              "critical_d0d2": statistics.mean(gev[k][1].elapsed_time(ends[k])
+                                               for k in range(args.steps))}
     value, ms = whole_job(ms, nvert, args.steps, dev)
 
     # end to end through the public API, the field coming from pinned host memory
@@ -464,6 +473,12 @@ def main():
                              "achieved_gbs": grad_bytes / (grad_ms / 1e3) / 1e9,
                              "peak_gbs": hbm_peak, "peak_kind": peak_kind,
                              "frac": grad_bytes / (grad_ms / 1e3) / 1e9 / hbm_peak}},
+        "stages_ms": stages,
+        # the same steps without the order stage (a user that already holds
+        # the order, or compares (key, vertex) pairs directly)
+        "excluding_order": {"ms_per_step": ms / args.steps - stages["order"],
+                            "value": nvert * world / ((ms / args.steps - stages["order"]) / 1e3),
+                            "unit": "vertices/s"},
         "gpu_launches": launches,
         "clocks": clocks,
         "e2e": e2e,

@@ -41,10 +41,31 @@ struct TileSmem {
 
 __device__ __forceinline__ void stage(TileSmem& sm, const uint8_t* desc, const uint64_t* rec,
                                       int64_t a0, int64_t n) {
-  for (int i = threadIdx.x; i < CTILE; i += CNT) {
-    int64_t a = a0 + i;
-    sm.rec[padded(i)] = a < n ? __ldg(reinterpret_cast<const unsigned long long*>(rec) + a) : 0ull;
-    sm.desc[padded(i)] = a < n ? __ldg(desc + a) : (uint8_t)0;
+  // whole tiles of aligned arrays move in 16-byte loads (the usual case:
+  // the library's own buffers); the ragged last tile and odd pointers
+  // element by element
+  const bool vec = ((reinterpret_cast<uintptr_t>(rec) | reinterpret_cast<uintptr_t>(desc)) & 15) == 0 &&
+                   a0 + CTILE <= n;
+  if (vec) {
+    const ulonglong2* r2 = reinterpret_cast<const ulonglong2*>(rec + a0);
+    for (int i = threadIdx.x; i < CTILE / 2; i += CNT) {
+      const ulonglong2 v = __ldg(r2 + i);
+      sm.rec[padded(2 * i)] = v.x;
+      sm.rec[padded(2 * i + 1)] = v.y;
+    }
+    const uint4* d4 = reinterpret_cast<const uint4*>(desc + a0);
+    for (int i = threadIdx.x; i < CTILE / 16; i += CNT) {
+      const uint4 v = __ldg(d4 + i);
+      const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int j = 0; j < 16; ++j) sm.desc[padded(16 * i + j)] = (uint8_t)(w[j >> 2] >> (8 * (j & 3)));
+    }
+  } else {
+    for (int i = threadIdx.x; i < CTILE; i += CNT) {
+      int64_t a = a0 + i;
+      sm.rec[padded(i)] = a < n ? __ldg(reinterpret_cast<const unsigned long long*>(rec) + a) : 0ull;
+      sm.desc[padded(i)] = a < n ? __ldg(desc + a) : (uint8_t)0;
+    }
   }
   __syncthreads();
 }

@@ -145,17 +145,38 @@ __global__ void __launch_bounds__(SORT_NT) upsweep_kernel(int pass, const Plan* 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < SORT_WARPS * 256; i += SORT_NT) (&h[0][0])[i] = 0;
   __syncthreads();
-  const int64_t base = (int64_t)blockIdx.x * SORT_TILE + (int64_t)warp * (32 * SORT_ITEMS);
-  for (int r = 0; r < SORT_ITEMS; ++r) {
-    int64_t i = base + r * 32 + lane;
-    uint32_t d = 256u + lane;  // unique dummy digit for the ragged tail
-    if (i < n) {
-      uint32_t k = 0, v = (uint32_t)i;
-      if (pass < 4) load_key(src, f, ka, kb, i, k);
-      else if (src != SRC_FIELD) v = __ldg((src == SRC_A ? va : vb) + i);
-      d = digit_of(pass, k, v, fl);
+  const int64_t tile0 = (int64_t)blockIdx.x * SORT_TILE;
+  const uint32_t* kp = src == SRC_FIELD ? reinterpret_cast<const uint32_t*>(f)
+                                        : (src == SRC_A ? ka : kb);
+  if (pass < 4 && tile0 + SORT_TILE <= n && (reinterpret_cast<uintptr_t>(kp) & 15) == 0) {
+    // a whole tile of key bits in 16-byte loads (counts need no order)
+    const uint4* k4 = reinterpret_cast<const uint4*>(kp + tile0);
+    for (int q = threadIdx.x; q < SORT_TILE / 4; q += SORT_NT) {
+      const uint4 w = __ldg(k4 + q);
+      const uint32_t b[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        uint32_t k = b[j];
+        if (src == SRC_FIELD) {
+          bool nan = false;
+          k = canon_key(__uint_as_float(k), &nan);
+        }
+        atomicAdd(&h[warp][(k >> (8 * pass)) & 255u], 1u);
+      }
     }
-    if (d < 256u) atomicAdd(&h[warp][d], 1u);  // counts only: no order needed
+  } else {
+    const int64_t base = tile0 + (int64_t)warp * (32 * SORT_ITEMS);
+    for (int r = 0; r < SORT_ITEMS; ++r) {
+      int64_t i = base + r * 32 + lane;
+      uint32_t d = 256u + lane;  // unique dummy digit for the ragged tail
+      if (i < n) {
+        uint32_t k = 0, v = (uint32_t)i;
+        if (pass < 4) load_key(src, f, ka, kb, i, k);
+        else if (src != SRC_FIELD) v = __ldg((src == SRC_A ? va : vb) + i);
+        d = digit_of(pass, k, v, fl);
+      }
+      if (d < 256u) atomicAdd(&h[warp][d], 1u);  // counts only: no order needed
+    }
   }
   __syncthreads();
   for (int d = threadIdx.x; d < 256; d += SORT_NT) {

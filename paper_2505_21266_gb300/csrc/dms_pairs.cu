@@ -1177,9 +1177,16 @@ __global__ void b_count_fields(const FieldTab ft, const Tri T, const int64_t* __
                                const int64_t* __restrict__ n_dev, int per_anchor,
                                unsigned long long* fcount) {
   const int64_t n = *n_dev;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    if (T.s[i].res != kNone) atomicAdd(fcount + field_of_vertex(ft, crit[i] / per_anchor), 1ull);
+  const int lane = threadIdx.x & 31;
+  // the saddles are in field order, so the lanes of a warp mostly share a
+  // field: one atomic per field present in the warp, not one per pair
+  for (int64_t base = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) - lane; base < n;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + lane;
+    const int f = (i < n && T.s[i].res != kNone) ? field_of_vertex(ft, crit[i] / per_anchor) : -1;
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, f);
+    if (f >= 0 && lane == __ffs(peers) - 1) atomicAdd(fcount + f, (unsigned long long)__popc(peers));
+  }
 }
 
 __global__ void b_field_offsets(const unsigned long long* __restrict__ fcount, int nfields,

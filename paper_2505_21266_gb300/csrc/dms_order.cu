@@ -10,8 +10,9 @@
 //     decision never leaves the device;
 //   * per pass: an upsweep counts digits per tile, a three-kernel exclusive
 //     scan turns the (digit-major) tile counts into output offsets, and a
-//     downsweep ranks the tile stably with warp match / popc, stages it in
-//     shared memory in digit order and writes it out;
+//     downsweep ranks the tile stably (the lanes holding the same digit from
+//     ballots on its bits, then popc), stages it in shared memory in digit
+//     order and writes it out;
 //   * the first active pass reads the float field itself (payload = index),
 //     the last one scatters order[payload] = position instead of writing keys.
 #include <algorithm>
@@ -310,7 +311,14 @@ __global__ void __launch_bounds__(SORT_NT, 4) downsweep_kernel(
       val[r] = src == SRC_FIELD ? (uint32_t)i : __ldg(vsrc + i);
       d = digit_of(pass, key[r], val[r], fl);
     }
-    unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
+    // lanes with the same digit: eight ballots on its bits and one on validity
+    unsigned peers = __ballot_sync(0xFFFFFFFFu, d < 256u);
+    if (d >= 256u) peers = ~peers;
+#pragma unroll
+    for (int bit = 0; bit < 8; ++bit) {
+      const unsigned bal = __ballot_sync(0xFFFFFFFFu, (d >> bit) & 1u);
+      peers &= ((d >> bit) & 1u) ? bal : ~bal;
+    }
     unsigned int b = d < 256u ? sm.wh[warp][d] : 0u;
     __syncwarp();
     pos[r] = (unsigned short)(b + __popc(peers & lt));

@@ -59,7 +59,7 @@ struct Smem {
   uint32_t win[3][WY][WX];
   unsigned long long recs[2][TY][TX];
   lowerstar::Keys<NT> keys;
-  uint16_t perm[(TX + 1) * (TY + 1)];  // slab vertices grouped by lower-star size
+  uint16_t perm[(TX + 1) * (TY + 1)];  // slab vertices grouped by bucket, largest first
   uint8_t kcnt[(TX + 1) * (TY + 1)];   // bucket: 16 x lower neighbours + lower tets (<= 15)
   uint16_t lmask[(TX + 1) * (TY + 1)];
   unsigned int bucket[256];
@@ -114,8 +114,9 @@ __device__ void gradient_tile(Smem<TY>& sm, const uint32_t* __restrict__ order, 
     const Row* wm = sm.win[(z + 2) % 3];
     const Row* w0 = sm.win[z % 3];
     const Row* wp = sm.win[(z + 1) % 3];
-    // group the slab's vertices by the size of their lower star so that the
-    // lanes of a warp get similar work; warps take groups largest-first
+    // group the slab's vertices by the trip counts of their lower-star loops
+    // so that the lanes of a warp get similar work; warps take groups
+    // largest-first
     for (int b = tid; b < 256; b += NT) sm.bucket[b] = 0;
     __syncthreads();
     for (int i = tid; i < nvx * nvy; i += NT) {

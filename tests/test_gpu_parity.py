@@ -139,3 +139,21 @@ def test_capacity_error_reports_counts():
     torch.cuda.synchronize()
     assert int(st.item()) & (1 << 4)
     assert [int(x) for x in counts.cpu()] == need
+
+
+def test_parity_structured_fields():
+    """Plateaus and periodic patterns over several tiles and z-chunks: a
+    constant field (every comparison decided by the vertex offset: one
+    critical simplex, no pairs), stripes along one axis, and a checkerboard
+    (a dense critical set: ~1/4 of the edges and triangles are critical)."""
+    def grid(shape):
+        return np.meshgrid(*[np.arange(s) for s in shape], indexing="ij")
+    z, y, x = grid((36, 50, 70))
+    const = np.zeros(z.shape, dtype=np.float32)
+    stripes = ((x // 3) % 4).astype(np.float32) - 1.5
+    z, y, x = grid((18, 34, 40))
+    checker = ((x + y + z) % 2).astype(np.float32)
+    for f in (const, stripes, checker):
+        _check_all(np.ascontiguousarray(f))
+    r = oracle.run(const)
+    assert [len(r.crit(d)) for d in range(4)] == [1, 0, 0, 0]

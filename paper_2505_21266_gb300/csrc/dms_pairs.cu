@@ -625,6 +625,48 @@ __global__ void round_merge(const uint32_t* __restrict__ live, const unsigned in
   }
 }
 
+// Minimum spanning forest first (Borůvka), then the pairing on its edges.
+// Alg. 1 pairs nothing at a saddle whose ends are already joined by lighter
+// saddles, and such a saddle changes no component: these are exactly the
+// saddles outside the minimum spanning forest of the extremum graph
+// (weights are distinct), so the pairing over the forest's edges alone is
+// the pairing over all saddles.  Borůvka rounds find the forest fast: every
+// component joins its neighbour across its lightest live saddle (that
+// saddle is a forest edge by the cut property), with no regard to ages, so
+// components at least halve per round and the saddles inside a component
+// drop out as loops.  The exact rounds then run on the forest's edges only.
+__global__ void boruvka_hook(const uint32_t* __restrict__ live, const unsigned int* __restrict__ live_n,
+                             Tri T, Nodes nd, uint64_t round, uint32_t* next, unsigned int* next_n,
+                             uint32_t* forest, unsigned int* forest_n) {
+  unsigned int n = *live_n;
+  for (unsigned int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const uint32_t i = live[j];
+    const uint32_t a = T.s[i].ra, b = T.s[i].rb;
+    if (a == b) continue;  // inside one component: not a forest edge
+    const unsigned long long tv = (round << 44) | (kMask44 - T.s[i].w);
+    const bool sa = a != nd.immortal && nd.best[a] == tv;
+    const bool sb = b != nd.immortal && nd.best[b] == tv;
+    if (!sa && !sb) {
+      append(next, next_n, i);
+      continue;
+    }
+    append(forest, forest_n, i);
+    // each component hooks under the other end of its own lightest saddle;
+    // two components that chose the same saddle hook one way only
+    if (sa && sb) nd.parent[min(a, b)] = max(a, b);
+    else if (sa) nd.parent[a] = b;
+    else nd.parent[b] = a;
+  }
+}
+
+__global__ void reset_nodes(Nodes nd, int64_t nnode) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nnode;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    nd.parent[i] = (uint32_t)i;
+    nd.best[i] = 0ull;
+  }
+}
+
 // The last few live saddles, processed one by one in increasing weight: the
 // lightest live saddle is always the lightest of both of its components, so
 // this continues Alg. 1 exactly.
@@ -777,7 +819,8 @@ __global__ void write_essential(const float* __restrict__ f, const uint32_t* __r
 struct DiagWs {
   Tri T0, T2;
   uint32_t *live0, *live1;
-  unsigned int* ctr;  // [0..1] live counts, [2] pair count
+  uint32_t* forest;  // the spanning-forest saddles found by the Borůvka rounds
+  unsigned int* ctr;  // [0..1] live counts, [2] forest count
   Nodes nd;  // union-find nodes: parent, best live saddle, age
   uint32_t* claim;  // one word per tet id: the dual walk that passed it
   int64_t nclaim;
@@ -797,6 +840,7 @@ DiagWs carve_diag(void* base, const int64_t* nc, int64_t nclaim) {
   w.T2 = w.T0;  // D0 and D2 run one after the other and share the arrays
   w.live0 = c.take<uint32_t>(nsad);
   w.live1 = c.take<uint32_t>(nsad);
+  w.forest = c.take<uint32_t>(nsad);
   w.ctr = c.take<unsigned int>(8);
   w.nd.parent = c.take<uint32_t>(nnode);
   w.nd.best = c.take<unsigned long long>(nnode);
@@ -811,11 +855,9 @@ DiagWs carve_diag(void* base, const int64_t* nc, int64_t nclaim) {
 
 constexpr unsigned int kSeqMax = 4096;  // live saddles left to the sequential finish
 
-int run_rounds(DiagWs& w, Tri T, cudaStream_t s, int32_t* dstatus) {
-  uint32_t* cur = w.live0;
-  uint32_t* nxt = w.live1;
-  unsigned int* cur_n = w.ctr + 0;
-  unsigned int* nxt_n = w.ctr + 1;
+// the exact rounds over the live list (cur, *cur_n), alternating with (nxt, *nxt_n)
+int run_rounds_from(DiagWs& w, Tri T, uint32_t* cur, unsigned int* cur_n, uint32_t* nxt,
+                    unsigned int* nxt_n, cudaStream_t s, int32_t* dstatus) {
   unsigned int prev = 0xFFFFFFFFu;
   for (uint64_t round = 1;; ++round) {
     unsigned int h = 0;
@@ -840,6 +882,39 @@ int run_rounds(DiagWs& w, Tri T, cudaStream_t s, int32_t* dstatus) {
   }
   (void)dstatus;
   return launch_status();
+}
+
+int run_rounds(DiagWs& w, Tri T, cudaStream_t s, int32_t* dstatus) {
+  return run_rounds_from(w, T, w.live0, w.ctr + 0, w.live1, w.ctr + 1, s, dstatus);
+}
+
+// Borůvka rounds over the live saddles in w.live0 (count ctr[0]) collect
+// the spanning forest's saddles; the node arrays are then reset and the
+// exact rounds pair the forest's saddles.
+int run_pairing(DiagWs& w, Tri T, int64_t nnode, cudaStream_t s, int32_t* dstatus) {
+  uint32_t* cur = w.live0;
+  uint32_t* nxt = w.live1;
+  unsigned int* cur_n = w.ctr + 0;
+  unsigned int* nxt_n = w.ctr + 1;
+  unsigned int* forest_n = w.ctr + 2;
+  DMS_CUDA_OK(cudaMemsetAsync(forest_n, 0, sizeof(unsigned int), s));
+  for (uint64_t round = 1;; ++round) {
+    unsigned int h = 0;
+    DMS_CUDA_OK(cudaMemcpyAsync(&h, cur_n, sizeof(h), cudaMemcpyDeviceToHost, s));
+    DMS_CUDA_OK(cudaStreamSynchronize(s));
+    if (h == 0) break;
+    if (round >= 64) return DMS_ERR_TIMEOUT;  // components at least halve per round
+    const unsigned int blocks = (unsigned int)std::min<int64_t>((h + 255) / 256, 1 << 16);
+    DMS_CUDA_OK(cudaMemsetAsync(nxt_n, 0, sizeof(unsigned int), s));
+    round_find<<<blocks, 256, 0, s>>>(cur, cur_n, T, w.nd, round); count_launch();
+    boruvka_hook<<<blocks, 256, 0, s>>>(cur, cur_n, T, w.nd, round, nxt, nxt_n, w.forest, forest_n); count_launch();
+    std::swap(cur, nxt);
+    std::swap(cur_n, nxt_n);
+  }
+  const unsigned int nb = (unsigned int)std::min<int64_t>((nnode + 255) / 256, 1 << 16);
+  reset_nodes<<<std::max(nb, 1u), 256, 0, s>>>(w.nd, nnode); count_launch();
+  // the forest's saddles are the live list of the exact rounds
+  return run_rounds_from(w, T, w.forest, forest_n, w.live0, w.ctr + 0, s, dstatus);
 }
 
 int write_diagram(int dim, DiagWs& w, const Dev& D, const float* f, const uint32_t* order,
@@ -897,7 +972,7 @@ int launch_diagram(const float* f, const uint32_t* order, const uint8_t* desc, c
     link_walks<<<nb(nc[1]), TB, 0, s>>>(nc[1], w.T0, w.live0, w.ctr + 0, dstatus); count_launch();
   }
   w.nd.immortal = kNone;  // every minimum but the global one can die
-  int st = run_rounds(w, w.T0, s, dstatus);
+  int st = run_pairing(w, w.T0, std::max<int64_t>(nc[0], 1), s, dstatus);
   if (st) return st;
   st = write_diagram(0, w, D, f, order, crit0, crit1, nc[1], d0, cap0, n_out + 0, dstatus, s);
   if (st) return st;
@@ -916,7 +991,7 @@ int launch_diagram(const float* f, const uint32_t* order, const uint8_t* desc, c
     link_walks<<<nb(nc[2]), TB, 0, s>>>(nc[2], w.T2, w.live0, w.ctr + 0, dstatus); count_launch();
   }
   w.nd.immortal = 0;  // OUTSIDE
-  st = run_rounds(w, w.T2, s, dstatus);
+  st = run_pairing(w, w.T2, nc[3] + 1, s, dstatus);
   if (st) return st;
   st = write_diagram(2, w, D, f, order, crit2, crit3, nc[2], d2, cap2, n_out + 1, dstatus, s);
   if (st) return st;

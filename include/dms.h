@@ -190,10 +190,14 @@ int dms_critical_noalloc(const uint8_t* desc, const uint64_t* rec, dms_dims d, i
  * two cofacets of every critical triangle the dual (ascending) v-path is
  * followed to a critical tetrahedron, or to a virtual OUTSIDE node when the
  * path leaves the grid; triangles are taken in decreasing order and the lower
- * maximum dies (OUTSIDE never dies).  The pairing runs in rounds that are
- * exact: a round merges every saddle that is the lightest live saddle of both
- * of its components, or the lightest of a component whose other side is
- * older; both choices are the ones Alg. 1 makes at that saddle's turn.
+ * maximum dies (OUTSIDE never dies).  Alg. 1 pairs nothing at a saddle whose
+ * ends lighter saddles already join, so only the saddles of the minimum
+ * spanning forest of the extremum graph matter: Boruvka rounds find them
+ * first (every component joins across its lightest live saddle).  The
+ * pairing then runs in rounds over those saddles that are exact: a round
+ * merges every saddle that is the lightest live saddle of both of its
+ * components, or the lightest of a component whose other side is older;
+ * both choices are the ones Alg. 1 makes at that saddle's turn.
  * Paths that meet share their tail: a walk that reaches a vertex (D0) or a
  * tetrahedron (D2) another walk has passed stops and takes that walk's end.
  *   f, order, desc, rec   as above;  crit0..3 and n_crit (HOST array of 4)
@@ -241,9 +245,11 @@ int dms_diagram_d0d2(const float* f, const uint32_t* order, const uint8_t* desc,
  *                (1 << DMS_ERR_CAPACITY); the call can then be repeated with
  *                larger capacities).
  *   ws           at least dms_batch_workspace_size(...) bytes.
- * The pairing runs at most dms_batch_max_rounds() rounds and then finishes at
- * most 4096 saddles in order; beyond that (1 << DMS_ERR_TIMEOUT) is set and
- * the per-field entry points should be used.
+ * The spanning forest takes a fixed 40 Boruvka rounds (enough: the active
+ * components at least halve per round); the pairing runs at most
+ * dms_batch_max_rounds() rounds and then finishes at most 4096 saddles in
+ * order; beyond that (1 << DMS_ERR_TIMEOUT) is set and the per-field entry
+ * points should be used.
  */
 int32_t dms_batch_tile_variants(void);
 int32_t dms_batch_max_rounds(void);

@@ -1182,6 +1182,23 @@ __global__ void b_d2_weights(const FieldTab ft, const uint32_t* __restrict__ ord
   }
 }
 
+// node arrays back to singletons between the forest and the pairing rounds
+// (node count on the device)
+__global__ void b_reset_nodes(Nodes nd, const int64_t* __restrict__ cnt, int64_t extra) {
+  const int64_t n = *cnt + extra;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    nd.parent[i] = (uint32_t)i;
+    nd.best[i] = 0ull;
+  }
+}
+
+// the fixed number of Borůvka rounds must have emptied the live list (they
+// do: active components at least halve per round)
+__global__ void b_forest_done(const unsigned int* __restrict__ live_n, int32_t* dstatus) {
+  if (threadIdx.x == 0 && blockIdx.x == 0 && *live_n != 0) set_status(dstatus, DMS_ERR_TIMEOUT);
+}
+
 __global__ void b_link_walks(const int64_t* __restrict__ n_dev, Tri T, uint32_t* live,
                              unsigned int* live_n, int32_t* dstatus) {
   const int64_t nt = *n_dev;
@@ -1359,6 +1376,7 @@ __global__ void __launch_bounds__(PNT) b_write_pairs(int dim, const FieldTab ft,
 }  // namespace
 
 constexpr int kBatchRounds = 96;
+constexpr int kBoruvkaRounds = 40;
 int diagram_batch_rounds() { return kBatchRounds; }
 
 // Workspace of the batched pairing: the DiagWs of the capacities plus the
@@ -1396,11 +1414,29 @@ int launch_diagram_batch(const float* f, const uint32_t* order, const uint8_t* d
   DMS_CUDA_OK(cudaMemsetAsync(fcount, 0, 2 * (nfields + 1) * sizeof(unsigned long long), s));
 
   bool mem_ok = true;
-  auto rounds = [&](Tri T) {
+  // the spanning forest by Borůvka rounds, then the exact rounds on its
+  // saddles (as in the single-field path), all with fixed round counts
+  auto rounds = [&](Tri T, const int64_t* ncnt, int64_t extra) {
     uint32_t* cur = w.live0;
     uint32_t* nxt = w.live1;
     unsigned int* cur_n = w.ctr + 0;
     unsigned int* nxt_n = w.ctr + 1;
+    unsigned int* forest_n = w.ctr + 2;
+    mem_ok = mem_ok && cudaMemsetAsync(forest_n, 0, sizeof(unsigned int), s) == cudaSuccess;
+    for (int r = 1; r <= kBoruvkaRounds; ++r) {
+      mem_ok = mem_ok && cudaMemsetAsync(nxt_n, 0, sizeof(unsigned int), s) == cudaSuccess;
+      round_find<<<G, TB, 0, s>>>(cur, cur_n, T, w.nd, (uint64_t)r); count_launch();
+      boruvka_hook<<<G, TB, 0, s>>>(cur, cur_n, T, w.nd, (uint64_t)r, nxt, nxt_n, w.forest,
+                                    forest_n); count_launch();
+      std::swap(cur, nxt);
+      std::swap(cur_n, nxt_n);
+    }
+    b_forest_done<<<1, 32, 0, s>>>(cur_n, dstatus); count_launch();
+    b_reset_nodes<<<G, TB, 0, s>>>(w.nd, ncnt, extra); count_launch();
+    cur = w.forest;
+    cur_n = forest_n;
+    nxt = w.live0;
+    nxt_n = w.ctr + 0;
     for (int r = 1; r <= kBatchRounds; ++r) {
       mem_ok = mem_ok && cudaMemsetAsync(nxt_n, 0, sizeof(unsigned int), s) == cudaSuccess;
       round_find<<<G, TB, 0, s>>>(cur, cur_n, T, w.nd, (uint64_t)r); count_launch();
@@ -1433,7 +1469,7 @@ int launch_diagram_batch(const float* f, const uint32_t* order, const uint8_t* d
   }
   b_link_walks<<<G, TB, 0, s>>>(cnt_dev + 1, w.T0, w.live0, w.ctr + 0, dstatus); count_launch();
   w.nd.immortal = kNone;
-  rounds(w.T0);
+  rounds(w.T0, cnt_dev + 0, 0);
   write(0, w.T0, crit[0], crit[1], cnt_dev + 1, d0, pair_offsets, pair_totals + 0, fcount);
 
   // ---- D2
@@ -1448,7 +1484,7 @@ int launch_diagram_batch(const float* f, const uint32_t* order, const uint8_t* d
   }
   b_link_walks<<<G, TB, 0, s>>>(cnt_dev + 2, w.T2, w.live0, w.ctr + 0, dstatus); count_launch();
   w.nd.immortal = 0;  // OUTSIDE, shared by all fields
-  rounds(w.T2);
+  rounds(w.T2, cnt_dev + 3, 1);
   write(2, w.T2, crit[2], crit[3], cnt_dev + 2, d2, pair_offsets + (nfields + 1), pair_totals + 1,
         fcount + (nfields + 1));
   if (!mem_ok) return DMS_ERR_CUDA;

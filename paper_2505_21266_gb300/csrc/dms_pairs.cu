@@ -635,27 +635,73 @@ __global__ void round_merge(const uint32_t* __restrict__ live, const unsigned in
 // saddle is a forest edge by the cut property), with no regard to ages, so
 // components at least halve per round and the saddles inside a component
 // drop out as loops.  The exact rounds then run on the forest's edges only.
-__global__ void boruvka_hook(const uint32_t* __restrict__ live, const unsigned int* __restrict__ live_n,
-                             Tri T, Nodes nd, uint64_t round, uint32_t* next, unsigned int* next_n,
-                             uint32_t* forest, unsigned int* forest_n) {
-  unsigned int n = *live_n;
-  for (unsigned int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-    const uint32_t i = live[j];
-    const uint32_t a = T.s[i].ra, b = T.s[i].rb;
-    if (a == b) continue;  // inside one component: not a forest edge
-    const unsigned long long tv = (round << 44) | (kMask44 - T.s[i].w);
-    const bool sa = a != nd.immortal && nd.best[a] == tv;
-    const bool sb = b != nd.immortal && nd.best[b] == tv;
-    if (!sa && !sb) {
-      append(next, next_n, i);
-      continue;
+// Appends of a whole CTA (256 threads) to two lists at once: one atomic per
+// list per CTA and pass -- a counter that every warp of the grid hits
+// serialises the appends of the first rounds, where almost every live
+// saddle is appended to one list or the other.  Every thread of the CTA
+// must call it.
+struct CtaAppend {
+  unsigned int off[2][8];
+  unsigned int base[2];
+};
+__device__ __forceinline__ void cta_append2(CtaAppend& sh, bool w0, uint32_t* l0, unsigned int* c0,
+                                            bool w1, uint32_t* l1, unsigned int* c1, uint32_t v) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned b0 = __ballot_sync(0xFFFFFFFFu, w0), b1 = __ballot_sync(0xFFFFFFFFu, w1);
+  if (lane == 0) {
+    sh.off[0][warp] = __popc(b0);
+    sh.off[1][warp] = __popc(b1);
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    const int k = threadIdx.x;
+    unsigned int t = 0;
+    for (int w = 0; w < 8; ++w) {
+      const unsigned int x = sh.off[k][w];
+      sh.off[k][w] = t;
+      t += x;
     }
-    append(forest, forest_n, i);
-    // each component hooks under the other end of its own lightest saddle;
-    // two components that chose the same saddle hook one way only
-    if (sa && sb) nd.parent[min(a, b)] = max(a, b);
-    else if (sa) nd.parent[a] = b;
-    else nd.parent[b] = a;
+    sh.base[k] = t ? atomicAdd(k ? c1 : c0, t) : 0u;
+  }
+  __syncthreads();
+  const unsigned lt = (1u << lane) - 1u;
+  if (w0) l0[sh.base[0] + sh.off[0][warp] + __popc(b0 & lt)] = v;
+  if (w1) l1[sh.base[1] + sh.off[1][warp] + __popc(b1 & lt)] = v;
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) boruvka_hook(const uint32_t* __restrict__ live,
+                                                    const unsigned int* __restrict__ live_n, Tri T,
+                                                    Nodes nd, uint64_t round, uint32_t* next,
+                                                    unsigned int* next_n, uint32_t* forest,
+                                                    unsigned int* forest_n) {
+  __shared__ CtaAppend sh;
+  const unsigned int n = *live_n;
+  // CTA-uniform passes: every thread reaches the appends
+  for (unsigned int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const unsigned int j = base + threadIdx.x;
+    bool wait = false, tree = false;
+    uint32_t i = 0;
+    if (j < n) {
+      i = live[j];
+      const uint32_t a = T.s[i].ra, b = T.s[i].rb;
+      if (a != b) {  // else inside one component: not a forest edge
+        const unsigned long long tv = (round << 44) | (kMask44 - T.s[i].w);
+        const bool sa = a != nd.immortal && nd.best[a] == tv;
+        const bool sb = b != nd.immortal && nd.best[b] == tv;
+        if (!sa && !sb) {
+          wait = true;
+        } else {
+          tree = true;
+          // each component hooks under the other end of its own lightest
+          // saddle; two components that chose the same saddle hook one way only
+          if (sa && sb) nd.parent[min(a, b)] = max(a, b);
+          else if (sa) nd.parent[a] = b;
+          else nd.parent[b] = a;
+        }
+      }
+    }
+    cta_append2(sh, wait, next, next_n, tree, forest, forest_n, i);
   }
 }
 

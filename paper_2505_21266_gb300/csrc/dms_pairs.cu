@@ -228,6 +228,41 @@ __device__ __forceinline__ void append(uint32_t* list, unsigned int* count, uint
   list[base + __popc(active & ((1u << lane) - 1u))] = v;
 }
 
+// Appends of a whole CTA (256 threads) to two lists at once: one atomic per
+// list per CTA and pass -- a counter that every warp of the grid hits
+// serialises the appends of the first rounds, where almost every live
+// saddle is appended to one list or the other.  Every thread of the CTA
+// must call it.
+struct CtaAppend {
+  unsigned int off[2][8];
+  unsigned int base[2];
+};
+__device__ __forceinline__ void cta_append2(CtaAppend& sh, bool w0, uint32_t* l0, unsigned int* c0,
+                                            bool w1, uint32_t* l1, unsigned int* c1, uint32_t v) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned b0 = __ballot_sync(0xFFFFFFFFu, w0), b1 = __ballot_sync(0xFFFFFFFFu, w1);
+  if (lane == 0) {
+    sh.off[0][warp] = __popc(b0);
+    sh.off[1][warp] = __popc(b1);
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    const int k = threadIdx.x;
+    unsigned int t = 0;
+    for (int w = 0; w < 8; ++w) {
+      const unsigned int x = sh.off[k][w];
+      sh.off[k][w] = t;
+      t += x;
+    }
+    sh.base[k] = t ? atomicAdd(k ? c1 : c0, t) : 0u;
+  }
+  __syncthreads();
+  const unsigned lt = (1u << lane) - 1u;
+  if (w0) l0[sh.base[0] + sh.off[0][warp] + __popc(b0 & lt)] = v;
+  if (w1) l1[sh.base[1] + sh.off[1][warp] + __popc(b1 & lt)] = v;
+  __syncthreads();
+}
+
 
 // D0: the weight of each critical edge (its lexicographic key).
 __global__ void d0_weights(Dev D, const uint32_t* __restrict__ order,
@@ -496,17 +531,22 @@ __global__ void __launch_bounds__(256) walk_each(const W wk, const int64_t* n_de
 // nodes; a saddle whose walks end at different nodes is live in the pairing.
 // (saddles marked in Sad::pad are left out of the pairing: on 2D grids the
 // D1 pass skips the edges D0 already paired)
-__global__ void link_walks(int64_t nt, Tri T, uint32_t* live, unsigned int* live_n,
-                           int32_t* dstatus, bool skip_marked = false) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= nt) return;
-  if (skip_marked && T.s[i].pad) return;
-  const uint32_t n0 = resolve_walk(T.s, T.s[i].ra, 2 * nt, dstatus);
-  const uint32_t n1 = resolve_walk(T.s, T.s[i].rb, 2 * nt, dstatus);
-  if (n0 == n1) return;
-  T.s[i].na = n0;
-  T.s[i].nb = n1;
-  append(live, live_n, (uint32_t)i);
+__global__ void __launch_bounds__(256) link_walks(int64_t nt, Tri T, uint32_t* live,
+                                                  unsigned int* live_n, int32_t* dstatus,
+                                                  bool skip_marked = false) {
+  __shared__ CtaAppend sh;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  bool keep = false;
+  if (i < nt && !(skip_marked && T.s[i].pad)) {
+    const uint32_t n0 = resolve_walk(T.s, T.s[i].ra, 2 * nt, dstatus);
+    const uint32_t n1 = resolve_walk(T.s, T.s[i].rb, 2 * nt, dstatus);
+    if (n0 != n1) {
+      T.s[i].na = n0;
+      T.s[i].nb = n1;
+      keep = true;
+    }
+  }
+  cta_append2(sh, keep, live, live_n, false, live, live_n, (uint32_t)i);
 }
 
 __global__ void init_nodes_d0(const uint32_t* __restrict__ order, const int64_t* __restrict__ crit0,
@@ -589,39 +629,47 @@ __global__ void round_find(const uint32_t* __restrict__ live, const unsigned int
 //    b's root, which is older than a's, so a's root is the younger one.
 // A root dies through its own lightest saddle only, so it dies at most once
 // per round, and the links never form a cycle (each points to an older root).
-__global__ void round_merge(const uint32_t* __restrict__ live, const unsigned int* __restrict__ live_n,
-                            Tri T, Nodes nd, uint64_t round, uint32_t* next,
-                            unsigned int* next_n) {
-  unsigned int n = *live_n;
-  for (unsigned int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-    uint32_t i = live[j];
-    uint32_t a = T.s[i].ra, b = T.s[i].rb;
-    if (a == b) continue;  // both ends already joined: no pair (Alg. 1, r0 == r1)
-    unsigned long long tv = (round << 44) | (kMask44 - T.s[i].w);
-    const bool la = a != nd.immortal && nd.best[a] == tv;
-    const bool lb = b != nd.immortal && nd.best[b] == tv;
-    if (!la && !lb) {  // the lightest live saddle of neither side: wait
-      append(next, next_n, i);
-      continue;
+__global__ void __launch_bounds__(256) round_merge(const uint32_t* __restrict__ live,
+                                                   const unsigned int* __restrict__ live_n, Tri T,
+                                                   Nodes nd, uint64_t round, uint32_t* next,
+                                                   unsigned int* next_n) {
+  __shared__ CtaAppend sh;
+  const unsigned int n = *live_n;
+  // CTA-uniform passes: every thread reaches the appends
+  for (unsigned int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const unsigned int j = base + threadIdx.x;
+    bool wait = false;
+    uint32_t i = 0;
+    if (j < n) {
+      i = live[j];
+      const uint32_t a = T.s[i].ra, b = T.s[i].rb;
+      if (a != b) {  // else both ends already joined: no pair (Alg. 1, r0 == r1)
+        const unsigned long long tv = (round << 44) | (kMask44 - T.s[i].w);
+        const bool la = a != nd.immortal && nd.best[a] == tv;
+        const bool lb = b != nd.immortal && nd.best[b] == tv;
+        uint32_t young = kNone, old = kNone;
+        if (la || lb) {
+          const uint64_t ga = nd.age[a], gb = nd.age[b];
+          if (la && lb) {
+            young = ga > gb ? a : b;
+            old = young == a ? b : a;
+          } else if (la && ga > gb) {
+            young = a;
+            old = b;
+          } else if (lb && gb > ga) {
+            young = b;
+            old = a;
+          }
+        }
+        if (young != kNone) {
+          nd.parent[young] = old;
+          T.s[i].res = young;
+        } else {
+          wait = true;  // the lightest live saddle of neither side, or uphill: wait
+        }
+      }
     }
-    const uint64_t ga = nd.age[a], gb = nd.age[b];
-    uint32_t young = kNone, old = kNone;
-    if (la && lb) {
-      young = ga > gb ? a : b;
-      old = young == a ? b : a;
-    } else if (la && ga > gb) {
-      young = a;
-      old = b;
-    } else if (lb && gb > ga) {
-      young = b;
-      old = a;
-    }
-    if (young != kNone) {
-      nd.parent[young] = old;
-      T.s[i].res = young;
-    } else {
-      append(next, next_n, i);
-    }
+    cta_append2(sh, wait, next, next_n, false, next, next_n, i);
   }
 }
 
@@ -635,41 +683,6 @@ __global__ void round_merge(const uint32_t* __restrict__ live, const unsigned in
 // saddle is a forest edge by the cut property), with no regard to ages, so
 // components at least halve per round and the saddles inside a component
 // drop out as loops.  The exact rounds then run on the forest's edges only.
-// Appends of a whole CTA (256 threads) to two lists at once: one atomic per
-// list per CTA and pass -- a counter that every warp of the grid hits
-// serialises the appends of the first rounds, where almost every live
-// saddle is appended to one list or the other.  Every thread of the CTA
-// must call it.
-struct CtaAppend {
-  unsigned int off[2][8];
-  unsigned int base[2];
-};
-__device__ __forceinline__ void cta_append2(CtaAppend& sh, bool w0, uint32_t* l0, unsigned int* c0,
-                                            bool w1, uint32_t* l1, unsigned int* c1, uint32_t v) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const unsigned b0 = __ballot_sync(0xFFFFFFFFu, w0), b1 = __ballot_sync(0xFFFFFFFFu, w1);
-  if (lane == 0) {
-    sh.off[0][warp] = __popc(b0);
-    sh.off[1][warp] = __popc(b1);
-  }
-  __syncthreads();
-  if (threadIdx.x < 2) {
-    const int k = threadIdx.x;
-    unsigned int t = 0;
-    for (int w = 0; w < 8; ++w) {
-      const unsigned int x = sh.off[k][w];
-      sh.off[k][w] = t;
-      t += x;
-    }
-    sh.base[k] = t ? atomicAdd(k ? c1 : c0, t) : 0u;
-  }
-  __syncthreads();
-  const unsigned lt = (1u << lane) - 1u;
-  if (w0) l0[sh.base[0] + sh.off[0][warp] + __popc(b0 & lt)] = v;
-  if (w1) l1[sh.base[1] + sh.off[1][warp] + __popc(b1 & lt)] = v;
-  __syncthreads();
-}
-
 __global__ void __launch_bounds__(256) boruvka_hook(const uint32_t* __restrict__ live,
                                                     const unsigned int* __restrict__ live_n, Tri T,
                                                     Nodes nd, uint64_t round, uint32_t* next,
@@ -1245,17 +1258,26 @@ __global__ void b_forest_done(const unsigned int* __restrict__ live_n, int32_t* 
   if (threadIdx.x == 0 && blockIdx.x == 0 && *live_n != 0) set_status(dstatus, DMS_ERR_TIMEOUT);
 }
 
-__global__ void b_link_walks(const int64_t* __restrict__ n_dev, Tri T, uint32_t* live,
-                             unsigned int* live_n, int32_t* dstatus) {
+__global__ void __launch_bounds__(256) b_link_walks(const int64_t* __restrict__ n_dev, Tri T,
+                                                    uint32_t* live, unsigned int* live_n,
+                                                    int32_t* dstatus) {
+  __shared__ CtaAppend sh;
   const int64_t nt = *n_dev;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nt;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t n0 = resolve_walk(T.s, T.s[i].ra, 2 * nt, dstatus);
-    const uint32_t n1 = resolve_walk(T.s, T.s[i].rb, 2 * nt, dstatus);
-    if (n0 == n1) continue;
-    T.s[i].na = n0;
-    T.s[i].nb = n1;
-    append(live, live_n, (uint32_t)i);
+  // CTA-uniform passes: every thread reaches the appends
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < nt;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    bool keep = false;
+    if (i < nt) {
+      const uint32_t n0 = resolve_walk(T.s, T.s[i].ra, 2 * nt, dstatus);
+      const uint32_t n1 = resolve_walk(T.s, T.s[i].rb, 2 * nt, dstatus);
+      if (n0 != n1) {
+        T.s[i].na = n0;
+        T.s[i].nb = n1;
+        keep = true;
+      }
+    }
+    cta_append2(sh, keep, live, live_n, false, live, live_n, (uint32_t)i);
   }
 }
 

@@ -218,15 +218,6 @@ __device__ __forceinline__ uint32_t resolve_walk(const Sad* __restrict__ sd, uin
   return x;
 }
 
-__device__ __forceinline__ void append(uint32_t* list, unsigned int* count, uint32_t v) {
-  unsigned int active = __activemask();
-  int lane = threadIdx.x & 31;
-  int leader = __ffs(active) - 1;
-  unsigned int base = 0;
-  if (lane == leader) base = atomicAdd(count, __popc(active));
-  base = __shfl_sync(active, base, leader);
-  list[base + __popc(active & ((1u << lane) - 1u))] = v;
-}
 
 // Appends of a whole CTA (256 threads) to two lists at once: one atomic per
 // list per CTA and pass -- a counter that every warp of the grid hits

@@ -218,7 +218,6 @@ __device__ __forceinline__ uint32_t resolve_walk(const Sad* __restrict__ sd, uin
   return x;
 }
 
-
 // Appends of a whole CTA (256 threads) to two lists at once: one atomic per
 // list per CTA and pass -- a counter that every warp of the grid hits
 // serialises the appends of the first rounds, where almost every live

@@ -154,3 +154,20 @@ def test_forest_is_kruskal_forest():
                 parent[a] = b
                 kruskal.append(i)
         assert sorted(_forest(t0, t1, len(rank), None)) == kruskal
+
+
+def test_schedule_on_the_worked_example():
+    """The extremum graph of the paper's self-correcting pairing figure
+    (Sec. 4.3, stored under tests/golden with its citation)."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "selfcorrecting_example.json")) as fh:
+        g = json.load(fh)
+    t = g["triplets"]
+    t0 = [x[1] for x in t]
+    t1 = [x[2] for x in t]
+    rank = list(range(g["n_extrema"]))
+    for forest_first in (True, False):
+        got = schedule(t0, t1, rank, forest_first=forest_first, seq_max=0)
+        assert {(t[j][0], got[j]) for j in range(len(t)) if got[j] >= 0} == \
+            {tuple(p) for p in g["pairs"]}

@@ -83,3 +83,22 @@ def test_batch_host_validation(lib):
     assert args(thin, 0, 1 << 40) == 2    # DMS_ERR_DIMS
     assert args(good, 3, 1 << 40) == 8    # no such tile variant
     assert args(good, 0, 16) == 5         # DMS_ERR_WORKSPACE
+
+
+def test_diagram_workspace_size_covers_its_parts(lib):
+    """The D0/D2 workspace holds, at least, one claim word per tetrahedron
+    id and, per saddle, its 32-byte record plus three 4-byte list entries
+    (two live lists and the spanning-forest list); it grows with the
+    saddle and extremum counts."""
+    from paper_2505_21266_gb300 import _lib
+    d = _lib.dms_dims(40, 50, 60)
+    n = 40 * 50 * 60
+
+    def size(c0, c1, c2, c3):
+        return lib.dms_diagram_workspace_size(d, (ctypes.c_int64 * 4)(c0, c1, c2, c3))
+
+    base = size(10, 100, 100, 10)
+    assert base >= 24 * n + 44 * 100
+    assert size(10, 100_000, 100, 10) - base >= 44 * (100_000 - 100)
+    assert size(10, 100, 100_000, 10) - base >= 44 * (100_000 - 100)
+    assert size(50_000, 100, 100, 10) > base  # union-find nodes

@@ -171,7 +171,10 @@ int dms_critical(const uint8_t* desc, const uint64_t* rec, dms_dims d, int64_t* 
  * dms_critical_noalloc_max_vertices() = 2^30 vertices return
  * DMS_ERR_TOO_LARGE.  The first call on a device looks up that device's
  * address of the array (cudaGetSymbolAddress), so make a first call on each
- * device before capturing streams.  Every call shares the array: calls whose
+ * device before capturing streams.  The looked-up address stays cached for
+ * the life of the process: after a cudaDeviceReset (or any other teardown of
+ * the device's primary context) the cached address is stale, so do not call
+ * this entry point on a device after resetting it.  Every call shares the array: calls whose
  * GPU work may overlap (other streams, other host threads) race on it.  The
  * array needs no clearing: each call writes all the scratch it reads.
  * Nothing is allocated (no cudaMalloc, cudaFree or allocating library call).

@@ -45,7 +45,9 @@ std::mutex g_mutex;
 void* g_scratch_ptr[kMaxDevices] = {};
 
 // The device address of g_scratch on the current device (looked up once per
-// device; the host-side symbol itself is not a device address).
+// device; the host-side symbol itself is not a device address).  The cache
+// is not refreshed: a cudaDeviceReset makes the cached address stale, which
+// the header documents as a restriction on callers.
 int scratch_for_current_device(void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DMS_ERR_CUDA;

@@ -63,3 +63,27 @@ def test_host_lower_star_fields(host_lib):
     _check(host_lib, fields.gaussian_mixture((20, 22, 24), 8, (0.05, 0.2), 1e-3, 1).numpy())
     _check(host_lib, fields.quantized_noise((18, 19, 20), 256, 3).numpy())
     _check(host_lib, fields.uniform01((16, 17, 18), 4).numpy())
+
+
+def test_host_lower_star_hand_worked_cases(host_lib):
+    """The kernel's restated pop order on the lower stars worked by hand from
+    the algorithm (tests/golden/lower_stars.json)."""
+    import refcomplex as rc
+    from test_oracle_pins import golden_lower_stars
+    cx = rc.Complex(3, 3, 3)
+    for name, f, x, exp_pairs, exp_crit in golden_lower_stars():
+        order = rc.canonical_order(f).astype(np.uint32)
+        desc = np.zeros(27, np.uint8)
+        rec = np.zeros(27, np.uint64)
+        assert lib_ok(host_lib, order, desc, rec)
+        pairs, crit = rd.decode(desc, rec, 3, 3, 3)
+        got = {tuple(int(v) for v in p) for p in pairs
+               if cx.max_vertex(cx.verts(int(p[0]), int(p[1])), order) == x}
+        assert got == exp_pairs, name
+        got_c = {(d, int(i)) for d in range(4) for i in crit[d]
+                 if cx.max_vertex(cx.verts(d, int(i)), order) == x}
+        assert got_c == exp_crit, name
+
+
+def lib_ok(lib, order, desc, rec):
+    return lib.host_gradient(order.ctypes.data, 3, 3, 3, desc.ctypes.data, rec.ctypes.data) == 0

@@ -452,3 +452,65 @@ def test_diagrams_are_stable_under_perturbation(seed):
         assert _bottleneck(a, b) <= eps + 1e-9
     ef, eg = rf.get(oracle.D0_ESSENTIAL), rg.get(oracle.D0_ESSENTIAL)
     assert abs(float(ef["birth"][0]) - float(eg["birth"][0])) <= eps + 1e-9
+
+
+# ------------------------------- hand-worked lower stars (Sec. 2.3) --------
+
+_NEIGHBOUR_OFFSETS = {
+    "X+": (1, 0, 0), "X-": (-1, 0, 0), "Y+": (0, 1, 0), "Y-": (0, -1, 0),
+    "Z+": (0, 0, 1), "Z-": (0, 0, -1), "XY+": (1, 1, 0), "XY-": (-1, -1, 0),
+    "XZ+": (1, 0, 1), "XZ-": (-1, 0, -1), "YZ+": (0, 1, 1), "YZ-": (0, -1, -1),
+    "D+": (1, 1, 1), "D-": (-1, -1, -1)}
+
+
+def golden_lower_stars():
+    """The cases of tests/golden/lower_stars.json as (name, field, expected
+    pairs as (tail_dim, tail_id, head_id), expected criticals as (dim, id))
+    on a 3x3x3 grid whose centre vertex is x; ids from refcomplex's own
+    restatement of the documented id convention."""
+    with open(os.path.join(GOLDEN, "lower_stars.json")) as fh:
+        g = json.load(fh)
+    cx = rc.Complex(3, 3, 3)
+    x = cx.vid(1, 1, 1)
+
+    def vertex(label):
+        if label == "x":
+            return x
+        dx, dy, dz = _NEIGHBOUR_OFFSETS[label]
+        return cx.vid(1 + dx, 1 + dy, 1 + dz)
+
+    def simplex(text):
+        s = tuple(sorted(vertex(t) for t in text.split()))
+        return len(s) - 1, cx.type_id(s)
+
+    out = []
+    for case in g["cases"]:
+        f = 100.0 + np.arange(27, dtype=np.float32)
+        f[x] = 50.0
+        for label, r in case["lower"].items():
+            f[vertex(label)] = 1.0 + r
+        pairs = set()
+        for tail, head in case["pairs"]:
+            (dt, it), (_, ih) = simplex(tail), simplex(head)
+            pairs.add((dt, it, ih))
+        crit = {simplex(t) for t in case["critical"]}
+        out.append((case["name"], f.reshape(3, 3, 3), x, pairs, crit))
+    return out
+
+
+@pytest.mark.parametrize("case", golden_lower_stars(), ids=lambda c: c[0])
+def test_lower_star_partners_match_hand_worked_cases(case):
+    """Which edge pairs with which triangle and which triangle with which tet
+    (the choice ProcessLowerStars makes, not only the critical counts),
+    against lower stars worked by hand from the algorithm's steps."""
+    name, f, x, exp_pairs, exp_crit = case
+    pairs, crit = oracle.lower_star_vertex(f, x)
+    assert {tuple(int(v) for v in row) for row in pairs} == exp_pairs, name
+    assert {(int(d), int(i)) for d, i in crit} == exp_crit, name
+    # the whole-grid run agrees on the lower star of x
+    r = oracle.run(f, diagrams=False)
+    cx = rc.Complex(3, 3, 3)
+    order = rc.canonical_order(f)
+    gp = {tuple(int(v) for v in row) for row in r.get(oracle.GRAD_PAIRS)
+          if cx.max_vertex(cx.verts(int(row[0]), int(row[1])), order) == x}
+    assert gp == exp_pairs, name

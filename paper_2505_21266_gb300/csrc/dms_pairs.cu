@@ -903,8 +903,13 @@ DiagWs carve_diag(void* base, const int64_t* nc, int64_t nclaim) {
 }
 
 constexpr unsigned int kSeqMax = 4096;  // live saddles left to the sequential finish
+constexpr uint64_t kMaxExactRounds = 256;  // then the sorted finish, whatever is left
 
-// the exact rounds over the live list (cur, *cur_n), alternating with (nxt, *nxt_n)
+// the exact rounds over the live list (cur, *cur_n), alternating with (nxt, *nxt_n).
+// A round that removes under 1/64 of the live saddles (a chain of components
+// merging one saddle per round, say) or the round limit hands what is left
+// to the sorted finish at once: it continues Alg. 1 exactly for any number
+// of saddles, so the number of host-synchronised rounds stays bounded.
 int run_rounds_from(DiagWs& w, Tri T, uint32_t* cur, unsigned int* cur_n, uint32_t* nxt,
                     unsigned int* nxt_n, cudaStream_t s, int32_t* dstatus) {
   unsigned int prev = 0xFFFFFFFFu;
@@ -913,8 +918,11 @@ int run_rounds_from(DiagWs& w, Tri T, uint32_t* cur, unsigned int* cur_n, uint32
     DMS_CUDA_OK(cudaMemcpyAsync(&h, cur_n, sizeof(h), cudaMemcpyDeviceToHost, s));
     DMS_CUDA_OK(cudaStreamSynchronize(s));
     if (h == 0) break;
-    if ((h <= kSeqMax && (uint64_t)h * 4 > (uint64_t)prev * 3) || round >= (1ull << 20) - 2) {
-      // few saddles left and the rounds have stalled: finish in sorted order
+    const bool stalled = (uint64_t)h * 4 > (uint64_t)prev * 3;     // < 1/4 removed
+    const bool crawling = (uint64_t)h * 64 > (uint64_t)prev * 63;  // < 1/64 removed
+    if ((h <= kSeqMax && stalled) || crawling || round >= kMaxExactRounds) {
+      // few saddles left and the rounds have stalled, or no real progress:
+      // finish in sorted order
       unsigned int blocks = (h + 255) / 256;
       gather_live<<<blocks, 256, 0, s>>>(cur, cur_n, T, w.rb.ka, w.rb.va); count_launch();
       bool in_a = radix64::sort(w.rb, h, 44, s);

@@ -17,6 +17,7 @@ the tests check the GPU against) on bounded crops of the same workload.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -59,16 +60,49 @@ def load_peaks():
     return 6800.0, 2070.0, "fallback"
 
 
-# The gradient kernel is bound by integer instruction issue, not by HBM (it
-# moves 13 B per vertex but executes ~140 warp instructions per vertex).  Its
-# roofline is the issue rate: SMs x 4 schedulers x 32 lanes x SM clock.  The
-# per-vertex figures below are those of the current kernel, from one ncu
-# capture of gradient_kernel on the same field recipe at 384^3 (summarised
-# under profiles/): smsp__inst_executed.sum / vertices, and
-# (dram__bytes_read.sum + dram__bytes_write.sum) / vertices.
-GRAD_WARP_INST_PER_VERTEX = 140.43
-GRAD_DRAM_BYTES_PER_VERTEX = 12.27
-GRAD_ALGO_BYTES_PER_VERTEX = 4 + 8 + 1  # read order, write record and desc
+# The gradient kernel's roofline is HBM: per vertex it reads the 4-byte order
+# and writes the 8-byte record and the 1-byte desc (13 B; the 4-byte critical
+# mask of the plan is not written, the critical bits live in the record).  It
+# is in fact bound by integer instruction issue, so the line also reports the
+# issue rate it fills.  Its per-vertex counters (warp instructions, DRAM
+# bytes) come from the committed ncu summary of the kernel, and are used only
+# when that summary was taken on the very sources being benchmarked (the
+# summary records a hash of them); otherwise they are reported as null.
+GRAD_ALGO_BYTES_PER_VERTEX = 4 + 8 + 1
+GRAD_PROFILE = os.path.join(ROOT, "profiles", "gradient_kernel_c3.md")
+GRAD_SOURCES = [os.path.join(ROOT, "paper_2505_21266_gb300", "csrc", n)
+                for n in ("dms_gradient.cu", "dms_lowerstar.cuh", "dms_star.cuh", "dms_common.cuh")]
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for p in GRAD_SOURCES:
+        with open(p, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profile_figures():
+    """The gradient kernel's per-vertex ncu figures from its committed
+    summary (a line 'figures: sources=<hash> warp_inst_per_vertex=<x>
+    dram_bytes_per_vertex=<y> ...'), or None when the summary is missing or
+    was taken on other sources."""
+    try:
+        with open(GRAD_PROFILE) as fh:
+            text = fh.read()
+    except OSError:
+        return None
+    for line in text.splitlines():
+        line = line.strip().strip("`")
+        if line.startswith("figures:"):
+            kv = dict(item.split("=", 1) for item in line[len("figures:"):].split() if "=" in item)
+            if kv.get("sources") != kernel_source_hash():
+                return None
+            try:
+                return {k: (v if k == "sources" else float(v)) for k, v in kv.items()}
+            except ValueError:
+                return None
+    return None
 
 
 class ClockSampler:
@@ -125,17 +159,39 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def host_threads() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
 def cpu_baseline(field_np: np.ndarray, crop: int):
-    """The oracle, as it stands, on a crop of the workload (one host core)."""
+    """The oracle, as it stands, on a crop of the workload: the whole path
+    with the lower stars of its gradient step spread over all host cores by
+    z-slabs (the paper's shared-memory parallel shape; the order and the D0/D2
+    pairing stay sequential, as in DMS), and the same path on one core; plus
+    the order + gradient steps alone on one core and on all cores."""
     import oracle
     oracle.build()
     sub = np.ascontiguousarray(field_np[:crop, :crop, :crop])
-    t0 = time.perf_counter()
-    oracle.run(sub)
-    dt = time.perf_counter() - t0
-    return {"value": sub.size / dt, "unit": "vertices/s", "cores": 1, "kind": "oracle",
-            "sample": f"full oracle path (order, gradient, critical, D0/D2) on a {crop}^3 crop "
-                      f"of the workload field, {dt:.1f} s"}
+    nthr = host_threads()
+
+    def timed(**kw):
+        t0 = time.perf_counter()
+        oracle.run(sub, **kw)
+        return time.perf_counter() - t0
+
+    t_all = timed(threads=nthr)
+    t_one = timed(threads=1)
+    g_one = timed(diagrams=False, threads=1)
+    g_all = timed(diagrams=False, threads=nthr)
+    return {"value": sub.size / t_all, "unit": "vertices/s", "cores": nthr, "kind": "oracle",
+            "sample": f"full oracle path (order, gradient on {nthr} threads by z-slabs, critical, "
+                      f"D0/D2) on a {crop}^3 crop of the workload field, {t_all:.1f} s",
+            "one_core": {"value": sub.size / t_one, "unit": "vertices/s", "seconds": t_one},
+            "order_gradient": {"one_core": sub.size / g_one, "all_cores": sub.size / g_all,
+                               "unit": "vertices/s", "threads": nthr}}
 
 
 def whole_job(ms_local: float, units_local: int, steps: int, device=None):
@@ -288,11 +344,12 @@ def run_reference(args):
     else:
         full = fields.mixture_crop(n, crop, 16, (0.05, 0.2), 1e-3, 0).numpy()
     f = np.ascontiguousarray(full, dtype=np.float32)
+    nthr = host_threads()
     for _ in range(args.warmup):
-        oracle.run(f)
+        oracle.run(f, threads=nthr)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.run(f)
+        oracle.run(f, threads=nthr)
     dt = time.perf_counter() - t0
     v = f.size * args.steps / dt
     line = {"metric": METRIC, "value": v, "unit": "vertices/s", "n_gpus": args.gpus,
@@ -300,8 +357,9 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "impl": "reference",
             "config": {"workload": wl["desc"], "sample": f"{crop}^3 crop per step"},
-            "cpu_baseline": {"value": v, "unit": "vertices/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{crop}^3 crop of the workload per step"},
+            "cpu_baseline": {"value": v, "unit": "vertices/s", "cores": nthr, "kind": "oracle",
+                             "sample": f"{crop}^3 crop of the workload per step, gradient "
+                                       f"on {nthr} threads by z-slabs"},
             "e2e": {"value": v, "unit": "vertices/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -315,7 +373,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
     ap.add_argument("--size", type=int, default=0, help="override the grid edge length")
-    ap.add_argument("--crop", type=int, default=80, help="oracle crop edge (CPU legs)")
+    ap.add_argument("--crop", type=int, default=64, help="oracle crop edge (CPU legs)")
+    ap.add_argument("--source-hash", action="store_true",
+                    help="print the hash of the gradient kernel's sources and exit")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-field batch leg")
@@ -324,6 +384,9 @@ def main():
     ap.add_argument("--leg", choices=["batched", "diff", "2d"], default=None,
                     help="run one comparison leg alone (its own JSON line), e.g. to profile it")
     args = ap.parse_args()
+    if args.source_hash:
+        print(kernel_source_hash())
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -449,9 +512,15 @@ def main():
     hbm_peak, sm_mhz, peak_kind = load_peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     issue_peak = sms * 4 * 32 * sm_mhz * 1e6 / 1e12  # lane-instructions/s, in T
-    grad_inst = GRAD_WARP_INST_PER_VERTEX * 32 * nvert
-    achieved = grad_inst / (grad_ms / 1e3) / 1e12
     grad_bytes = GRAD_ALGO_BYTES_PER_VERTEX * nvert
+    grad_gbs = grad_bytes / (grad_ms / 1e3) / 1e9
+    fig = profile_figures() if args.workload == "c3" else None
+    issue = None
+    if fig and "warp_inst_per_vertex" in fig:
+        ach = fig["warp_inst_per_vertex"] * 32 * nvert / (grad_ms / 1e3) / 1e12
+        issue = {"achieved": ach, "peak": issue_peak, "unit": "Tinst/s (lane-instructions)",
+                 "frac": ach / issue_peak, "warp_inst_per_vertex": fig["warp_inst_per_vertex"],
+                 "peak_kind": f"derived: {sms} SMs x 4 schedulers x 32 lanes x {sm_mhz:.0f} MHz"}
     line = {
         "metric": METRIC, "value": value, "unit": "vertices/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -461,18 +530,18 @@ def main():
                    "l2": "inputs (4 GiB field, 4 GiB order) larger than L2, no flush",
                    "critical": crit_counts, "pairs_d0_d2": n_pairs,
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "alu", "kernel": "gradient_kernel", "achieved": achieved,
-                     "peak": issue_peak, "unit": "Tinst/s (lane-instructions)",
-                     "frac": achieved / issue_peak,
-                     "peak_kind": f"derived: {sms} SMs x 4 x 32 lanes x {sm_mhz:.0f} MHz",
-                     # the per-vertex figures were measured on the 1024^3 recipe
-                     "traffic": GRAD_DRAM_BYTES_PER_VERTEX * nvert if args.workload == "c3" else None,
-                     "figures_from": "ncu capture of gradient_kernel, 384^3 field of the c3 recipe",
-                     "kernel_ms": grad_ms, "warp_inst_per_vertex": GRAD_WARP_INST_PER_VERTEX,
-                     "hbm": {"algorithmic_bytes": grad_bytes,
-                             "achieved_gbs": grad_bytes / (grad_ms / 1e3) / 1e9,
-                             "peak_gbs": hbm_peak, "peak_kind": peak_kind,
-                             "frac": grad_bytes / (grad_ms / 1e3) / 1e9 / hbm_peak}},
+        "roofline": {"bound": "hbm", "kernel": "gradient_kernel", "achieved": grad_gbs,
+                     "peak": hbm_peak, "unit": "GB/s", "frac": grad_gbs / hbm_peak,
+                     "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_vertex": GRAD_ALGO_BYTES_PER_VERTEX,
+                     "kernel_ms": grad_ms,
+                     # DRAM bytes per vertex of the committed ncu summary of
+                     # these very sources, scaled to this launch (null if none)
+                     "traffic": fig["dram_bytes_per_vertex"] * nvert
+                     if fig and "dram_bytes_per_vertex" in fig else None,
+                     "figures_from": os.path.relpath(GRAD_PROFILE, ROOT) if fig else None,
+                     "sources": kernel_source_hash(),
+                     "issue": issue},
         "stages_ms": stages,
         # the same steps without the order stage (a user that already holds
         # the order, or compares (key, vertex) pairs directly)

@@ -49,7 +49,7 @@ def build(force: bool = False) -> str:
             return _LIB
         os.makedirs(_BUILD, exist_ok=True)
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", _SRC, _SRC2,
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-pthread", _SRC, _SRC2,
                                "-o", tmp])
         os.replace(tmp, _LIB)
         return _LIB
@@ -62,6 +62,8 @@ def _load():
         i64, vp = ctypes.c_int64, ctypes.c_void_p
         lib.orc_run.restype = vp
         lib.orc_run.argtypes = [vp, i64, i64, i64, ctypes.c_int]
+        lib.orc_run_threads.restype = vp
+        lib.orc_run_threads.argtypes = [vp, i64, i64, i64, ctypes.c_int, ctypes.c_int]
         lib.orc_status.restype = ctypes.c_int
         lib.orc_status.argtypes = [vp]
         lib.orc_count.restype = i64
@@ -105,13 +107,14 @@ _DTYPES = {ORDER: np.uint32, D0: PAIR_DTYPE, D2: PAIR_DTYPE, D0_ESSENTIAL: PAIR_
 class Result:
     """Everything the oracle computed for one field (kept in C++ memory)."""
 
-    def __init__(self, field: np.ndarray, flags: int):
+    def __init__(self, field: np.ndarray, flags: int, threads: int = 1):
         f = np.ascontiguousarray(field, dtype=np.float32)
         if f.ndim != 3:
             raise ValueError("field must be 3D, indexed [z, y, x]")
         self.nz, self.ny, self.nx = f.shape
         lib = _load()
-        self._h = lib.orc_run(f.ctypes.data, self.nx, self.ny, self.nz, flags)
+        self._h = lib.orc_run_threads(f.ctypes.data, self.nx, self.ny, self.nz, flags,
+                                      int(threads))
         st = lib.orc_status(self._h)
         if st:
             lib.orc_free(self._h)
@@ -147,10 +150,14 @@ class Result:
             self._h = None
 
 
-def run(field: np.ndarray, order=True, gradient=True, diagrams=True, reduction=False) -> Result:
+def run(field: np.ndarray, order=True, gradient=True, diagrams=True, reduction=False,
+        threads: int = 1) -> Result:
+    """The oracle on one field.  ``threads`` > 1 spreads the lower stars of
+    the gradient step over host threads by z-slabs (same result); every
+    other step is single-threaded."""
     flags = (RUN_ORDER if order else 0) | (RUN_GRADIENT if gradient else 0) \
         | (RUN_DIAGRAMS if diagrams else 0) | (RUN_REDUCTION if reduction else 0)
-    return Result(field, flags)
+    return Result(field, flags, threads)
 
 
 def pair_extrema_saddles(t0, t1, rank) -> np.ndarray:

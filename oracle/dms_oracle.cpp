@@ -35,6 +35,7 @@
 #include <deque>
 #include <limits>
 #include <queue>
+#include <thread>
 #include <unordered_map>
 #include <utility>
 #include <vector>
@@ -452,7 +453,28 @@ void compute_order(Context& c) {
   for (int64_t r = 0; r < c.g.n; ++r) c.order[idx[r]] = uint32_t(r);
 }
 
-void compute_gradient(Context& c) {
+// The pairs and critical simplices of the lower stars of the vertices
+// [begin, end), in vertex order.
+struct LowerStarsOut {
+  std::vector<int64_t> pairs, crits;
+};
+void lower_stars_range(const Grid& g, const uint32_t* order, int64_t begin, int64_t end,
+                       LowerStarsOut* out) {
+  OrderLookup ol;
+  ol.order = order;
+  for (int64_t x = begin; x < end; ++x) {
+    LowerStarRun run{g, x, lower_star(g, ol, x), {}, {}};
+    run.run();
+    out->pairs.insert(out->pairs.end(), run.pairs.begin(), run.pairs.end());
+    out->crits.insert(out->crits.end(), run.crits.begin(), run.crits.end());
+  }
+}
+
+// threads > 1 runs the (independent) lower stars of z-slabs on that many
+// host threads -- the shared-memory parallel shape of the gradient step the
+// paper describes -- and merges their results in slab order; the result is
+// the same for any thread count.
+void compute_gradient(Context& c, int threads = 1) {
   const Grid& g = c.g;
   for (int d = 0; d < 4; ++d) {
     c.grad.p[d].assign(g.n * kTypes[d], kAbsent);
@@ -461,22 +483,31 @@ void compute_gradient(Context& c) {
       if (simplex_vertices(g, d, id, v)) c.grad.p[d][id] = kUnset;
     }
   }
-  OrderLookup ol;
-  ol.order = c.order.data();
-  for (int64_t x = 0; x < g.n; ++x) {
-    LowerStarRun run{g, x, lower_star(g, ol, x), {}, {}};
-    run.run();
-    for (size_t i = 0; i < run.pairs.size(); i += 3) {
-      int td = int(run.pairs[i]);
-      int64_t tail = run.pairs[i + 1], head = run.pairs[i + 2];
+  const int64_t nt = std::max<int64_t>(1, std::min<int64_t>(threads, g.nz));
+  std::vector<LowerStarsOut> parts(nt);
+  if (nt == 1) {
+    lower_stars_range(g, c.order.data(), 0, g.n, &parts[0]);
+  } else {
+    std::vector<std::thread> pool;
+    for (int64_t t = 0; t < nt; ++t) {
+      const int64_t z0 = g.nz * t / nt, z1 = g.nz * (t + 1) / nt;
+      pool.emplace_back(lower_stars_range, std::cref(g), c.order.data(), z0 * g.nx * g.ny,
+                        z1 * g.nx * g.ny, &parts[t]);
+    }
+    for (auto& th : pool) th.join();
+  }
+  for (const LowerStarsOut& part : parts) {
+    for (size_t i = 0; i < part.pairs.size(); i += 3) {
+      int td = int(part.pairs[i]);
+      int64_t tail = part.pairs[i + 1], head = part.pairs[i + 2];
       if (c.grad.p[td][tail] != kUnset || c.grad.p[td + 1][head] != kUnset) { c.status = 91; return; }
       c.grad.p[td][tail] = (head << 1) | 1;
       c.grad.p[td + 1][head] = (tail << 1) | 0;
     }
-    for (size_t i = 0; i < run.crits.size(); i += 2) {
-      int d = int(run.crits[i]);
-      if (c.grad.p[d][run.crits[i + 1]] != kUnset) { c.status = 91; return; }
-      c.grad.p[d][run.crits[i + 1]] = kCritical;
+    for (size_t i = 0; i < part.crits.size(); i += 2) {
+      int d = int(part.crits[i]);
+      if (c.grad.p[d][part.crits[i + 1]] != kUnset) { c.status = 91; return; }
+      c.grad.p[d][part.crits[i + 1]] = kCritical;
     }
   }
   for (int d = 0; d < 4; ++d) {
@@ -790,7 +821,15 @@ enum {
 // flags for orc_run
 enum { ORC_RUN_ORDER = 1, ORC_RUN_GRADIENT = 2, ORC_RUN_DIAGRAMS = 4, ORC_RUN_REDUCTION = 8 };
 
+// as orc_run, with the lower stars of the gradient step spread over
+// `threads` host threads (the other steps stay single-threaded)
+void* orc_run_threads(const float* f, int64_t nx, int64_t ny, int64_t nz, int flags, int threads);
+
 void* orc_run(const float* f, int64_t nx, int64_t ny, int64_t nz, int flags) {
+  return orc_run_threads(f, nx, ny, nz, flags, 1);
+}
+
+void* orc_run_threads(const float* f, int64_t nx, int64_t ny, int64_t nz, int flags, int threads) {
   Context* c = new Context;
   c->g = {nx, ny, nz, nx * ny * nz};
   if (!valid_dims(nx, ny, nz)) { c->status = 2; return c; }
@@ -799,7 +838,7 @@ void* orc_run(const float* f, int64_t nx, int64_t ny, int64_t nz, int flags) {
     if (std::isnan(v)) { c->status = 3; return c; }
   compute_order(*c);
   if (flags & (ORC_RUN_GRADIENT | ORC_RUN_DIAGRAMS)) {
-    compute_gradient(*c);
+    compute_gradient(*c, threads);
     if (c->status) return c;
   }
   if (flags & ORC_RUN_DIAGRAMS) {

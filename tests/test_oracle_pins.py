@@ -514,3 +514,15 @@ def test_lower_star_partners_match_hand_worked_cases(case):
     gp = {tuple(int(v) for v in row) for row in r.get(oracle.GRAD_PAIRS)
           if cx.max_vertex(cx.verts(int(row[0]), int(row[1])), order) == x}
     assert gp == exp_pairs, name
+
+
+def test_threaded_gradient_equals_single_threaded(rng):
+    """The CPU baseline's shape -- the lower stars of z-slabs on several host
+    threads -- gives the oracle's single-threaded result exactly."""
+    f = rng.integers(0, 7, size=(9, 8, 10)).astype(np.float32)
+    a = oracle.run(f)
+    b = oracle.run(f, threads=4)
+    for w in (oracle.GRAD_PAIRS, oracle.CRIT0, oracle.CRIT1, oracle.CRIT2, oracle.CRIT3):
+        assert np.array_equal(a.get(w), b.get(w))
+    for w in (oracle.D0, oracle.D2):
+        assert a.get(w).tobytes() == b.get(w).tobytes()

@@ -223,6 +223,28 @@ int dms_diagram_d0d2(const float* f, const uint32_t* order, const uint8_t* desc,
                      int64_t cap2, dms_pair* d0_essential, int64_t* n_out, void* ws,
                      size_t ws_bytes, int32_t* dstatus, void* stream);
 
+/* dms_diagram_d0d2_selfcorrecting -- the same D0 / D2 pairs (same arguments,
+ * workspace and outputs as dms_diagram_d0d2), paired by the paper's
+ * self-correcting pairing (Sec. 4.3, Alg. 4) run as a fixpoint instead of
+ * the spanning forest and exact rounds: every round, every saddle of the
+ * extremum graph computes the representatives of its two ends by following
+ * only links that earlier saddles (in Alg. 1's order) assigned -- each
+ * extremum's representative records the saddle that assigned it -- and the
+ * younger representative dies at the earliest saddle that claims it
+ * (atomicMin); wrong claims from stale links are corrected in later rounds.
+ * The rounds stop when no link changes; the result is Alg. 1's.  A chain of
+ * components that Alg. 1 merges one by one takes one round per merge; past
+ * 65536 rounds the call returns DMS_ERR_TIMEOUT.  Synchronises `stream`
+ * once per round (it reads the number of changed links on the host).
+ */
+int dms_diagram_d0d2_selfcorrecting(const float* f, const uint32_t* order, const uint8_t* desc,
+                                    const uint64_t* rec, dms_dims d, const int64_t* crit0,
+                                    const int64_t* crit1, const int64_t* crit2,
+                                    const int64_t* crit3, const int64_t* n_crit, dms_pair* d0,
+                                    int64_t cap0, dms_pair* d2, int64_t cap2,
+                                    dms_pair* d0_essential, int64_t* n_out, void* ws,
+                                    size_t ws_bytes, int32_t* dstatus, void* stream);
+
 /* ---------------------------------------------------------------- batch ---
  * dms_batch_diagrams -- (i)-(iv) for many fields of uneven dims at once
  * (the batch processing the paper contrasts with its per-dataset runs,

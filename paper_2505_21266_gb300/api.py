@@ -153,8 +153,13 @@ class Diagrams:
 
 
 def diagram_d0d2(field: torch.Tensor, order_t: torch.Tensor, g: Gradient, crit,
-                 status: torch.Tensor | None = None) -> Diagrams:
-    """D0 and D2 pairs (Sec. 2.5, Alg. 1 and its dual; Sec. 4)."""
+                 status: torch.Tensor | None = None, pairing: str = "rounds") -> Diagrams:
+    """D0 and D2 pairs (Sec. 2.5, Alg. 1 and its dual; Sec. 4).  ``pairing``
+    picks the parallel form of Alg. 1: "rounds" (spanning forest, then exact
+    rounds; the default) or "selfcorrecting" (the paper's self-correcting
+    pairing, Alg. 4, as a fixpoint); both give Alg. 1's pairs."""
+    if pairing not in ("rounds", "selfcorrecting"):
+        raise ValueError("pairing is 'rounds' or 'selfcorrecting'")
     _require_cuda(field, "field", torch.float32)
     lib = _lib.load()
     dev = field.device
@@ -169,10 +174,10 @@ def diagram_d0d2(field: torch.Tensor, order_t: torch.Tensor, g: Gradient, crit,
     ws = _ws(lib.dms_diagram_workspace_size(d, ncarr), dev)
     st = status if status is not None else torch.zeros(1, dtype=torch.int32, device=dev)
     crit_p = [_ptr(c) if c.numel() else None for c in crit]
-    _check(lib.dms_diagram_d0d2(_ptr(field), _ptr(order_t), _ptr(g.desc), _ptr(g.rec), d,
-                                *crit_p, ncarr, _ptr(d0), cap0, _ptr(d2), cap2, _ptr(ess),
-                                _ptr(n_out), _ptr(ws), ws.numel(), _ptr(st), _stream(dev)),
-           "dms_diagram_d0d2")
+    fn = lib.dms_diagram_d0d2 if pairing == "rounds" else lib.dms_diagram_d0d2_selfcorrecting
+    _check(fn(_ptr(field), _ptr(order_t), _ptr(g.desc), _ptr(g.rec), d, *crit_p, ncarr, _ptr(d0),
+              cap0, _ptr(d2), cap2, _ptr(ess), _ptr(n_out), _ptr(ws), ws.numel(), _ptr(st),
+              _stream(dev)), "dms_diagram_d0d2")
     if status is None:
         _device_status_check(st, "dms_diagram_d0d2")
     n = [int(x) for x in n_out.cpu()]
@@ -187,12 +192,12 @@ class Result:
     diagrams: Diagrams
 
 
-def diagram(field: torch.Tensor) -> Result:
+def diagram(field: torch.Tensor, pairing: str = "rounds") -> Result:
     """The whole hot path: order -> gradient -> critical simplices -> D0/D2."""
     o = order(field)
     g = gradient(o)
     c = critical(g)
-    dg = diagram_d0d2(field, o, g, c)
+    dg = diagram_d0d2(field, o, g, c, pairing=pairing)
     return Result(o, g, c, dg)
 
 

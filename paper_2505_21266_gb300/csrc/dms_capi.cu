@@ -19,7 +19,7 @@ int launch_diagram(const float* f, const uint32_t* order, const uint8_t* desc, c
                    const Grid& g, const int64_t* crit0, const int64_t* crit1, const int64_t* crit2,
                    const int64_t* crit3, const int64_t* nc, dms_pair* d0, int64_t cap0,
                    dms_pair* d2, int64_t cap2, dms_pair* ess, int64_t* n_out, void* ws,
-                   int32_t* dstatus, cudaStream_t s);
+                   int32_t* dstatus, cudaStream_t s, int pairing);
 int launch_backward(const dms_pair* pairs, int64_t n, const float* g, const Grid& grid,
                     float* grad, int32_t* dstatus, cudaStream_t s);
 long long& launch_counter() {
@@ -104,12 +104,12 @@ size_t dms_diagram_workspace_size(dms_dims d, const int64_t* n_crit) {
   return dms::diagram_workspace_bytes(g, n_crit);
 }
 
-int dms_diagram_d0d2(const float* f, const uint32_t* order, const uint8_t* desc,
-                     const uint64_t* rec, dms_dims d, const int64_t* crit0,
-                     const int64_t* crit1, const int64_t* crit2, const int64_t* crit3,
-                     const int64_t* n_crit, dms_pair* d0, int64_t cap0, dms_pair* d2,
-                     int64_t cap2, dms_pair* d0_essential, int64_t* n_out, void* ws,
-                     size_t ws_bytes, int32_t* dstatus, void* stream) {
+static int diagram_d0d2(const float* f, const uint32_t* order, const uint8_t* desc,
+                        const uint64_t* rec, dms_dims d, const int64_t* crit0,
+                        const int64_t* crit1, const int64_t* crit2, const int64_t* crit3,
+                        const int64_t* n_crit, dms_pair* d0, int64_t cap0, dms_pair* d2,
+                        int64_t cap2, dms_pair* d0_essential, int64_t* n_out, void* ws,
+                        size_t ws_bytes, int32_t* dstatus, void* stream, int pairing) {
   Grid g;
   if (!dms::make_grid(d, &g)) return DMS_ERR_DIMS;
   if (!f || !order || !desc || !rec || !n_crit || !d0_essential || !n_out || !ws || !dstatus)
@@ -127,7 +127,28 @@ int dms_diagram_d0d2(const float* f, const uint32_t* order, const uint8_t* desc,
   if (ws_bytes < dms::diagram_workspace_bytes(g, n_crit)) return DMS_ERR_WORKSPACE;
   return dms::launch_diagram(f, order, desc, rec, g, crit0, crit1, crit2, crit3, n_crit, d0, cap0,
                              d2, cap2, d0_essential, n_out, ws, dstatus,
-                             static_cast<cudaStream_t>(stream));
+                             static_cast<cudaStream_t>(stream), pairing);
+}
+
+int dms_diagram_d0d2(const float* f, const uint32_t* order, const uint8_t* desc,
+                     const uint64_t* rec, dms_dims d, const int64_t* crit0,
+                     const int64_t* crit1, const int64_t* crit2, const int64_t* crit3,
+                     const int64_t* n_crit, dms_pair* d0, int64_t cap0, dms_pair* d2,
+                     int64_t cap2, dms_pair* d0_essential, int64_t* n_out, void* ws,
+                     size_t ws_bytes, int32_t* dstatus, void* stream) {
+  return diagram_d0d2(f, order, desc, rec, d, crit0, crit1, crit2, crit3, n_crit, d0, cap0, d2,
+                      cap2, d0_essential, n_out, ws, ws_bytes, dstatus, stream, 0);
+}
+
+int dms_diagram_d0d2_selfcorrecting(const float* f, const uint32_t* order, const uint8_t* desc,
+                                    const uint64_t* rec, dms_dims d, const int64_t* crit0,
+                                    const int64_t* crit1, const int64_t* crit2,
+                                    const int64_t* crit3, const int64_t* n_crit, dms_pair* d0,
+                                    int64_t cap0, dms_pair* d2, int64_t cap2,
+                                    dms_pair* d0_essential, int64_t* n_out, void* ws,
+                                    size_t ws_bytes, int32_t* dstatus, void* stream) {
+  return diagram_d0d2(f, order, desc, rec, d, crit0, crit1, crit2, crit3, n_crit, d0, cap0, d2,
+                      cap2, d0_essential, n_out, ws, ws_bytes, dstatus, stream, 1);
 }
 
 int dms_backward(const dms_pair* pairs, int64_t n, const float* g, dms_dims d, float* grad,

@@ -871,6 +871,10 @@ struct DiagWs {
   uint32_t* forest;  // the spanning-forest saddles found by the Borůvka rounds
   unsigned int* ctr;  // [0..1] live counts, [2] forest count
   Nodes nd;  // union-find nodes: parent, best live saddle, age
+  // the self-correcting pairing's next links (the current ones live in
+  // nd.parent and nd.best)
+  uint32_t* sc_parent;
+  unsigned long long* sc_w;
   uint32_t* claim;  // one word per tet id: the dual walk that passed it
   int64_t nclaim;
   radix64::Buffers rb;
@@ -895,6 +899,8 @@ DiagWs carve_diag(void* base, const int64_t* nc, int64_t nclaim) {
   w.nd.best = c.take<unsigned long long>(nnode);
   w.nd.age = c.take<uint64_t>(nnode);
   w.nd.immortal = kNone;
+  w.sc_parent = c.take<uint32_t>(nnode);
+  w.sc_w = c.take<unsigned long long>(nnode);
   w.nclaim = nclaim;
   w.claim = c.take<uint32_t>(w.nclaim);
   w.rb = radix64::carve(c, std::max<int64_t>(nsad, 4096));
@@ -974,6 +980,134 @@ int run_pairing(DiagWs& w, Tri T, int64_t nnode, cudaStream_t s, int32_t* dstatu
   return run_rounds_from(w, T, w.forest, forest_n, w.live0, w.ctr + 0, s, dstatus);
 }
 
+// ---------------------------------------------------------------------------
+// The paper's self-correcting pairing (Sec. 4.3, Alg. 4) as a GPU fixpoint,
+// an alternative to the Borůvka forest + exact rounds above.
+//
+// Every extremum e holds a link (parent, saddle): the root it was merged
+// into and the saddle that merged it -- the representative of Alg. 4 that
+// also records the saddle which assigned it.  Every round, every live
+// saddle sigma (all of them at once, as Alg. 4 runs all its triplets)
+// computes the representatives of its two ends by following only links
+// set by saddles that come before sigma in Alg. 1's order (earlier links
+// exist at sigma's turn, later ones would not), with no path compression;
+// if they differ, the younger one dies at sigma, and of several saddles
+// that kill the same extremum the earliest wins (atomicMin of the weight).
+// The links of the next round are exactly those winning claims.  A saddle
+// whose representatives were computed from wrong links is recomputed in the
+// next round -- the self-correction of Alg. 4 -- and by induction on the
+// saddle order the k earliest saddles are right after k rounds, so the
+// rounds stop, when no link changes, at Alg. 1's pairs.  The node arrays
+// hold the current links: nd.parent (the parent, the node itself if none)
+// and nd.best (the linking saddle's weight, kNoLink if none).
+// ---------------------------------------------------------------------------
+constexpr unsigned long long kNoLink = ~0ull;
+
+__device__ __forceinline__ uint32_t sc_find(const Nodes& nd, uint32_t t, uint64_t w,
+                                            uint32_t limit, int32_t* dstatus) {
+  for (uint32_t it = 0; it <= limit; ++it) {
+    if (nd.best[t] >= w) return t;  // no link, or one set by a later saddle
+    t = nd.parent[t];
+  }
+  set_status(dstatus, DMS_ERR_TIMEOUT);  // links form no cycle: not reached
+  return t;
+}
+
+__global__ void sc_reset(Nodes nd, unsigned long long* nw, int64_t nnode) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nnode;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    nd.parent[i] = (uint32_t)i;
+    nd.best[i] = kNoLink;
+    nw[i] = kNoLink;
+  }
+}
+
+// representatives of both ends as of each saddle's turn; claim the younger
+__global__ void sc_claim(const uint32_t* __restrict__ live, const unsigned int* __restrict__ live_n,
+                         Tri T, Nodes nd, unsigned long long* nw, uint32_t nnode, int32_t* dstatus) {
+  const unsigned int n = *live_n;
+  for (unsigned int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const uint32_t i = live[j];
+    const uint64_t w = T.s[i].w;
+    const uint32_t a = sc_find(nd, T.s[i].na, w, nnode, dstatus);
+    const uint32_t b = sc_find(nd, T.s[i].nb, w, nnode, dstatus);
+    if (a == b) {  // both ends already joined at this saddle's turn: no pair
+      T.s[i].ra = kNone;
+      continue;
+    }
+    const uint32_t young = nd.age[a] > nd.age[b] ? a : b;
+    T.s[i].ra = young;
+    T.s[i].rb = young == a ? b : a;
+    atomicMin(nw + young, (unsigned long long)w);
+  }
+}
+
+// the winning claims become the next round's links
+__global__ void sc_link(const uint32_t* __restrict__ live, const unsigned int* __restrict__ live_n,
+                        Tri T, uint32_t* np, const unsigned long long* __restrict__ nw) {
+  const unsigned int n = *live_n;
+  for (unsigned int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const uint32_t i = live[j];
+    const uint32_t young = T.s[i].ra;
+    if (young != kNone && nw[young] == T.s[i].w) np[young] = T.s[i].rb;
+  }
+}
+
+// current <- next; counts the nodes whose link changed
+__global__ void sc_commit(Nodes nd, uint32_t* np, unsigned long long* nw, int64_t nnode,
+                          unsigned int* changed) {
+  unsigned int c = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nnode;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long w = nw[i];
+    const uint32_t p = w == kNoLink ? (uint32_t)i : np[i];
+    if (w != nd.best[i] || p != nd.parent[i]) ++c;
+    nd.best[i] = w;
+    nd.parent[i] = p;
+    nw[i] = kNoLink;
+  }
+  c = __reduce_add_sync(0xFFFFFFFFu, c);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(changed, c);
+}
+
+// the pair of each live saddle from the final links
+__global__ void sc_result(const uint32_t* __restrict__ live, const unsigned int* __restrict__ live_n,
+                          Tri T, Nodes nd) {
+  const unsigned int n = *live_n;
+  for (unsigned int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const uint32_t i = live[j];
+    const uint32_t young = T.s[i].ra;
+    T.s[i].res = (young != kNone && nd.best[young] == T.s[i].w) ? young : kNone;
+  }
+}
+
+constexpr int kMaxSelfCorrectingRounds = 1 << 16;
+
+int run_selfcorrecting(DiagWs& w, Tri T, int64_t nnode, cudaStream_t s, int32_t* dstatus) {
+  unsigned int* live_n = w.ctr + 0;
+  unsigned int* changed = w.ctr + 3;
+  unsigned int h = 0;
+  DMS_CUDA_OK(cudaMemcpyAsync(&h, live_n, sizeof(h), cudaMemcpyDeviceToHost, s));
+  DMS_CUDA_OK(cudaStreamSynchronize(s));
+  const unsigned int nb = (unsigned int)std::min<int64_t>((nnode + 255) / 256, 1 << 16);
+  sc_reset<<<std::max(nb, 1u), 256, 0, s>>>(w.nd, w.sc_w, nnode); count_launch();
+  if (h == 0) return launch_status();
+  const unsigned int blocks = (unsigned int)std::min<int64_t>((h + 255) / 256, 1 << 16);
+  for (int round = 1;; ++round) {
+    if (round > kMaxSelfCorrectingRounds) return DMS_ERR_TIMEOUT;
+    DMS_CUDA_OK(cudaMemsetAsync(changed, 0, sizeof(unsigned int), s));
+    sc_claim<<<blocks, 256, 0, s>>>(w.live0, live_n, T, w.nd, w.sc_w, (uint32_t)nnode, dstatus); count_launch();
+    sc_link<<<blocks, 256, 0, s>>>(w.live0, live_n, T, w.sc_parent, w.sc_w); count_launch();
+    sc_commit<<<std::max(nb, 1u), 256, 0, s>>>(w.nd, w.sc_parent, w.sc_w, nnode, changed); count_launch();
+    unsigned int c = 0;
+    DMS_CUDA_OK(cudaMemcpyAsync(&c, changed, sizeof(c), cudaMemcpyDeviceToHost, s));
+    DMS_CUDA_OK(cudaStreamSynchronize(s));
+    if (c == 0) break;
+  }
+  sc_result<<<blocks, 256, 0, s>>>(w.live0, live_n, T, w.nd); count_launch();
+  return launch_status();
+}
+
 int write_diagram(int dim, DiagWs& w, const Dev& D, const float* f, const uint32_t* order,
                   const int64_t* critA, const int64_t* critB, int64_t nsad, dms_pair* out,
                   int64_t cap, int64_t* n_out, int32_t* dstatus, cudaStream_t s) {
@@ -1002,7 +1136,7 @@ int launch_diagram(const float* f, const uint32_t* order, const uint8_t* desc, c
                    const Grid& g, const int64_t* crit0, const int64_t* crit1, const int64_t* crit2,
                    const int64_t* crit3, const int64_t* nc, dms_pair* d0, int64_t cap0,
                    dms_pair* d2, int64_t cap2, dms_pair* ess, int64_t* n_out, void* ws,
-                   int32_t* dstatus, cudaStream_t s) {
+                   int32_t* dstatus, cudaStream_t s, int pairing) {
   DiagWs w = carve_diag(ws, nc, 6 * g.n);
   Dev D;
   D.g = g;
@@ -1029,7 +1163,8 @@ int launch_diagram(const float* f, const uint32_t* order, const uint8_t* desc, c
     link_walks<<<nb(nc[1]), TB, 0, s>>>(nc[1], w.T0, w.live0, w.ctr + 0, dstatus); count_launch();
   }
   w.nd.immortal = kNone;  // every minimum but the global one can die
-  int st = run_pairing(w, w.T0, std::max<int64_t>(nc[0], 1), s, dstatus);
+  int st = pairing == 1 ? run_selfcorrecting(w, w.T0, std::max<int64_t>(nc[0], 1), s, dstatus)
+                        : run_pairing(w, w.T0, std::max<int64_t>(nc[0], 1), s, dstatus);
   if (st) return st;
   st = write_diagram(0, w, D, f, order, crit0, crit1, nc[1], d0, cap0, n_out + 0, dstatus, s);
   if (st) return st;
@@ -1048,7 +1183,8 @@ int launch_diagram(const float* f, const uint32_t* order, const uint8_t* desc, c
     link_walks<<<nb(nc[2]), TB, 0, s>>>(nc[2], w.T2, w.live0, w.ctr + 0, dstatus); count_launch();
   }
   w.nd.immortal = 0;  // OUTSIDE
-  st = run_pairing(w, w.T2, nc[3] + 1, s, dstatus);
+  st = pairing == 1 ? run_selfcorrecting(w, w.T2, nc[3] + 1, s, dstatus)
+                    : run_pairing(w, w.T2, nc[3] + 1, s, dstatus);
   if (st) return st;
   st = write_diagram(2, w, D, f, order, crit2, crit3, nc[2], d2, cap2, n_out + 1, dstatus, s);
   if (st) return st;

@@ -171,3 +171,66 @@ def test_schedule_on_the_worked_example():
         got = schedule(t0, t1, rank, forest_first=forest_first, seq_max=0)
         assert {(t[j][0], got[j]) for j in range(len(t)) if got[j] >= 0} == \
             {tuple(p) for p in g["pairs"]}
+
+
+# ------------------------------------------- self-correcting pairing (Alg. 4) --
+
+def _self_correcting(t0, t1, rank, max_rounds=10000):
+    """The fixpoint form of the paper's self-correcting pairing (Sec. 4.3,
+    Alg. 4) as the GPU runs it: every round every triplet j finds the
+    representatives of its ends by following only links assigned by
+    earlier triplets (each link records the triplet that assigned it), with
+    no path compression; the younger representative is claimed, the earliest
+    claimant of an extremum wins, and the winning claims are the next
+    round's links.  Returns (per-triplet result, rounds)."""
+    n = len(rank)
+    link = [None] * n  # (parent, triplet)
+
+    def find(t, j):
+        while link[t] is not None and link[t][1] < j:
+            t = link[t][0]
+        return t
+
+    for rounds in range(1, max_rounds + 1):
+        claim = {}
+        for j in range(len(t0)):
+            a, b = find(t0[j], j), find(t1[j], j)
+            if a == b:
+                continue
+            young, old = (a, b) if rank[a] > rank[b] else (b, a)
+            if young not in claim or j < claim[young][1]:
+                claim[young] = (old, j)
+        nxt = [claim.get(e) for e in range(n)]
+        if nxt == link:
+            break
+        link = nxt
+    res = [-1] * len(t0)
+    for e in range(n):
+        if link[e] is not None:
+            res[link[e][1]] = e
+    return res, rounds
+
+
+def test_self_correcting_fixpoint_equals_alg1(rng):
+    for _ in range(200):
+        n = int(rng.integers(2, 40))
+        m = int(rng.integers(1, 90))
+        t0 = [int(v) for v in rng.integers(0, n, m)]
+        t1 = [int(v) for v in rng.integers(0, n, m)]
+        rank = [int(v) for v in rng.permutation(n)]
+        res, _ = _self_correcting(t0, t1, rank)
+        assert res == [int(v) for v in oracle.pair_extrema_saddles(t0, t1, rank)]
+
+
+def test_self_correcting_on_chains():
+    """Chains of minima: each saddle's representatives come from following
+    the earlier saddles' links, so whichever end is older the fixpoint
+    settles in a few rounds (where the exact rounds above take one round
+    per merge when the minima deepen along the chain)."""
+    n = 40
+    t0 = list(range(n - 1))
+    t1 = list(range(1, n))
+    for rank in (list(range(n - 1, -1, -1)), list(range(n))):
+        res, rounds = _self_correcting(t0, t1, rank)
+        assert res == [int(v) for v in oracle.pair_extrema_saddles(t0, t1, rank)]
+        assert rounds <= 3

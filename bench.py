@@ -491,6 +491,29 @@ def main():
                                                for k in range(args.steps))}
     value, ms = whole_job(ms, nvert, args.steps, dev)
 
+    # the D0/D2 stage under the two parallel forms of Alg. 1: the default
+    # (spanning forest, then exact rounds) and the paper's self-correcting
+    # pairing (Alg. 4) as a fixpoint, on the same gradient
+    pairing_cmp = None
+    if world == 1:
+        o_ = dms.order(f)
+        g_ = dms.gradient(o_)
+        c_ = dms.critical(g_)
+        pairing_cmp = {}
+        for mode in ("rounds", "selfcorrecting"):
+            dms.diagram_d0d2(f, o_, g_, c_, pairing=mode)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            reps = max(1, min(args.steps, 3))
+            for _ in range(reps):
+                dms.diagram_d0d2(f, o_, g_, c_, pairing=mode)
+            b.record(stream)
+            torch.cuda.synchronize()
+            pairing_cmp[f"{mode}_ms"] = a.elapsed_time(b) / reps
+        pairing_cmp["note"] = "D0/D2 stage only (walks, pairing, pair lists) on the step's gradient"
+        del o_, g_, c_
+
     # end to end through the public API, the field coming from pinned host memory
     e2e = None
     if not args.no_e2e:
@@ -548,6 +571,7 @@ def main():
         "excluding_order": {"ms_per_step": ms / args.steps - stages["order"],
                             "value": nvert * world / ((ms / args.steps - stages["order"]) / 1e3),
                             "unit": "vertices/s"},
+        "d0d2_pairing": pairing_cmp,
         "gpu_launches": launches,
         "clocks": clocks,
         "e2e": e2e,

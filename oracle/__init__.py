@@ -31,7 +31,8 @@ _lib = None
 # output selectors (mirror the enum in dms_oracle.cpp)
 ORDER, CRIT0, CRIT1, CRIT2, CRIT3, GRAD_PAIRS, D0, D2, D0_ESSENTIAL = range(9)
 D0_TRIPLETS, D2_TRIPLETS, PARTNER0, PARTNER1, PARTNER2, PARTNER3, REDUCTION = range(9, 16)
-RUN_ORDER, RUN_GRADIENT, RUN_DIAGRAMS, RUN_REDUCTION = 1, 2, 4, 8
+D1 = 16
+RUN_ORDER, RUN_GRADIENT, RUN_DIAGRAMS, RUN_REDUCTION, RUN_D1 = 1, 2, 4, 8, 16
 
 ABSENT = -2
 CRITICAL = -1
@@ -99,9 +100,12 @@ class OracleError(RuntimeError):
 
 
 _STATUS = {2: "bad dims (each >= 2, fewer than 2^32 - 1 vertices)", 3: "NaN in the field",
-           90: "a simplex was left unclassified", 91: "a simplex was classified twice"}
+           90: "a simplex was left unclassified", 91: "a simplex was classified twice",
+           92: "D1: the highest edge of a boundary is paired with a vertex",
+           93: "D1: the highest edge of a boundary is a D0 death"}
 
-_DTYPES = {ORDER: np.uint32, D0: PAIR_DTYPE, D2: PAIR_DTYPE, D0_ESSENTIAL: PAIR_DTYPE}
+_DTYPES = {ORDER: np.uint32, D0: PAIR_DTYPE, D2: PAIR_DTYPE, D0_ESSENTIAL: PAIR_DTYPE,
+           D1: PAIR_DTYPE}
 
 
 class Result:
@@ -151,12 +155,14 @@ class Result:
 
 
 def run(field: np.ndarray, order=True, gradient=True, diagrams=True, reduction=False,
-        threads: int = 1) -> Result:
+        threads: int = 1, d1: bool = False) -> Result:
     """The oracle on one field.  ``threads`` > 1 spreads the lower stars of
     the gradient step over host threads by z-slabs (same result); every
-    other step is single-threaded."""
+    other step is single-threaded.  ``d1`` adds the saddle-saddle pairs
+    (Alg. 2-3, after D0 and D2)."""
     flags = (RUN_ORDER if order else 0) | (RUN_GRADIENT if gradient else 0) \
-        | (RUN_DIAGRAMS if diagrams else 0) | (RUN_REDUCTION if reduction else 0)
+        | (RUN_DIAGRAMS if diagrams else 0) | (RUN_REDUCTION if reduction else 0) \
+        | (RUN_D1 if d1 else 0)
     return Result(field, flags, threads)
 
 

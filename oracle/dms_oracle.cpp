@@ -35,6 +35,7 @@
 #include <deque>
 #include <limits>
 #include <queue>
+#include <set>
 #include <thread>
 #include <unordered_map>
 #include <utility>
@@ -438,7 +439,7 @@ struct Context {
   std::vector<int64_t> crit[4];
   std::vector<int64_t> grad_pairs;  // (tail_dim, tail_id, head_id) triples
   std::vector<int64_t> d0_trip, d2_trip;  // (saddle, t0, t1) in visiting order
-  std::vector<PairOut> d0, d2;
+  std::vector<PairOut> d0, d2, d1;
   PairOut d0_essential;
   std::vector<int64_t> red_pairs;  // (birth_dim, birth_id, death_id); death -1 = essential
 };
@@ -668,6 +669,101 @@ void compute_d2(Context& c) {
 }
 
 // ---------------------------------------------------------------------------
+// D1: the saddle-saddle pairs (Sec. 2.5, "D1 pairing"; Alg. 2 and Alg. 3),
+// taken sequentially -- the critical triangles in increasing order, so the
+// parallel case of Alg. 3 (a pair to be undone) never arises.
+//
+// Only the critical edges that D0 left unpaired and the critical triangles
+// that D2 left unpaired take part (the stratification of Sec. 2.5).  For a
+// triangle sigma, its boundary starts as the three edges of sigma; while it
+// is not empty, its highest edge tau (lexicographic key) is looked at: a
+// non-critical tau is paired with a triangle by the gradient, whose boundary
+// is added (mod 2: the homologous propagation); a critical tau that no
+// earlier triangle took is sigma's birth, and the pair (tau, sigma) is made;
+// a critical tau already taken by an earlier triangle sigma_tau has that
+// triangle's (final) boundary added.  The boundary of sigma is kept for the
+// triangles that come after it.
+// ---------------------------------------------------------------------------
+void compute_d1(Context& c) {
+  const Grid& g = c.g;
+  OrderLookup order;
+  order.order = c.order.data();
+  // edge key: orders of its vertices, higher first (lexicographic)
+  auto edge_key = [&](int64_t e) -> uint64_t {
+    int64_t v[4];
+    simplex_vertices(g, 1, e, v);
+    uint32_t a = order[v[0]], b = order[v[1]];
+    return (uint64_t(std::max(a, b)) << 32) | std::min(a, b);
+  };
+  auto triangle_edges = [&](int64_t t, int64_t out[3]) {
+    int64_t v[4];
+    simplex_vertices(g, 2, t, v);
+    for (int drop = 0; drop < 3; ++drop) {
+      int64_t f[2];
+      int k = 0;
+      for (int i = 0; i < 3; ++i)
+        if (i != drop) f[k++] = v[i];
+      out[drop] = simplex_id(g, 2, f);
+    }
+  };
+  std::vector<bool> in_d0(g.n * 7, false), in_d2(g.n * 12, false);
+  for (const PairOut& p : c.d0) in_d0[p.death_id] = true;
+  for (const PairOut& p : c.d2) in_d2[p.birth_id] = true;
+  // the unpaired critical triangles, increasing
+  std::vector<std::pair<std::vector<uint32_t>, int64_t>> sig;
+  for (int64_t t : c.crit[2]) {
+    if (in_d2[t]) continue;
+    int64_t v[4];
+    simplex_vertices(g, 2, t, v);
+    sig.push_back({key_of(order, 3, v), t});
+  }
+  std::sort(sig.begin(), sig.end(),
+            [](const std::pair<std::vector<uint32_t>, int64_t>& a,
+               const std::pair<std::vector<uint32_t>, int64_t>& b) {
+              return key_less(a.first, b.first);
+            });
+  typedef std::set<std::pair<uint64_t, int64_t>> Chain;  // (key, edge id)
+  std::unordered_map<int64_t, int64_t> pair_of_edge;       // critical edge -> its triangle
+  std::unordered_map<int64_t, Chain> boundary_of;          // triangle -> its final boundary
+  auto toggle = [](Chain& ch, const std::pair<uint64_t, int64_t>& e) {
+    auto it = ch.find(e);
+    if (it == ch.end()) ch.insert(e);
+    else ch.erase(it);
+  };
+  for (const auto& st : sig) {
+    const int64_t sigma = st.second;
+    Chain ch;
+    int64_t te[3];
+    triangle_edges(sigma, te);
+    for (int i = 0; i < 3; ++i) toggle(ch, {edge_key(te[i]), te[i]});
+    while (!ch.empty()) {
+      const int64_t tau = std::prev(ch.end())->second;
+      const int64_t p = c.grad.p[1][tau];
+      if (p != kCritical) {
+        if (p < 0 || !(p & 1)) { c.status = 92; return; }  // the highest edge of a cycle
+        int64_t pe[3];                                       // is never paired with a vertex
+        triangle_edges(p >> 1, pe);
+        for (int i = 0; i < 3; ++i) toggle(ch, {edge_key(pe[i]), pe[i]});
+        continue;
+      }
+      if (in_d0[tau]) { c.status = 93; return; }  // nor a D0 death
+      auto it = pair_of_edge.find(tau);
+      if (it == pair_of_edge.end()) {
+        pair_of_edge[tau] = sigma;
+        int64_t ev[4], sv[4];
+        simplex_vertices(g, 1, tau, ev);
+        simplex_vertices(g, 2, sigma, sv);
+        int64_t eb = max_vertex(order, 2, ev), sb = max_vertex(order, 3, sv);
+        c.d1.push_back({tau, sigma, c.f[eb], c.f[sb], uint32_t(eb), uint32_t(sb)});
+        break;
+      }
+      for (const auto& e : boundary_of[it->second]) toggle(ch, e);
+    }
+    boundary_of[sigma] = ch;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Z2 boundary-matrix reduction of the whole lexicographic filtration
 // (standard column algorithm; Sec. 2.4-2.5 define the pairs it yields).
 // ---------------------------------------------------------------------------
@@ -816,10 +912,12 @@ enum {
   ORC_PARTNER2 = 13,
   ORC_PARTNER3 = 14,
   ORC_REDUCTION = 15,   // int64 (birth_dim, birth_id, death_id or -1)
+  ORC_D1 = 16,          // 32-byte pair records (edge, triangle), in triangle order
 };
 
 // flags for orc_run
-enum { ORC_RUN_ORDER = 1, ORC_RUN_GRADIENT = 2, ORC_RUN_DIAGRAMS = 4, ORC_RUN_REDUCTION = 8 };
+enum { ORC_RUN_ORDER = 1, ORC_RUN_GRADIENT = 2, ORC_RUN_DIAGRAMS = 4, ORC_RUN_REDUCTION = 8,
+       ORC_RUN_D1 = 16 };
 
 // as orc_run, with the lower stars of the gradient step spread over
 // `threads` host threads (the other steps stay single-threaded)
@@ -841,9 +939,13 @@ void* orc_run_threads(const float* f, int64_t nx, int64_t ny, int64_t nz, int fl
     compute_gradient(*c, threads);
     if (c->status) return c;
   }
-  if (flags & ORC_RUN_DIAGRAMS) {
+  if (flags & (ORC_RUN_DIAGRAMS | ORC_RUN_D1)) {
     compute_d0(*c);
     compute_d2(*c);
+  }
+  if (flags & ORC_RUN_D1) {
+    compute_d1(*c);
+    if (c->status) return c;
   }
   if (flags & ORC_RUN_REDUCTION) compute_reduction(*c);
   return c;
@@ -867,6 +969,7 @@ int64_t orc_count(void* h, int what) {
     case ORC_PARTNER0: case ORC_PARTNER1: case ORC_PARTNER2: case ORC_PARTNER3:
       return (int64_t)c->grad.p[what - ORC_PARTNER0].size();
     case ORC_REDUCTION: return (int64_t)c->red_pairs.size();
+    case ORC_D1: return (int64_t)c->d1.size();
   }
   return -1;
 }
@@ -888,6 +991,7 @@ void orc_copy(void* h, int what, void* dst) {
     case ORC_PARTNER0: case ORC_PARTNER1: case ORC_PARTNER2: case ORC_PARTNER3:
       std::memcpy(dst, c->grad.p[what - ORC_PARTNER0].data(), n * 8); break;
     case ORC_REDUCTION: std::memcpy(dst, c->red_pairs.data(), n * 8); break;
+    case ORC_D1: std::memcpy(dst, c->d1.data(), n * sizeof(PairOut)); break;
   }
 }
 

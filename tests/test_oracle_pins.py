@@ -526,3 +526,33 @@ def test_threaded_gradient_equals_single_threaded(rng):
         assert np.array_equal(a.get(w), b.get(w))
     for w in (oracle.D0, oracle.D2):
         assert a.get(w).tobytes() == b.get(w).tobytes()
+
+
+# ------------------------------------------------------------ D1 (Alg. 2-3) --
+
+@pytest.mark.parametrize("shape", [(2, 2, 2), (4, 5, 3), (7, 6, 8), (12, 12, 12)])
+def test_d1_equals_boundary_matrix_reduction(rng, shape):
+    """The oracle's D1 (homologous propagation over the critical triangles
+    D2 left unpaired, Sec. 2.5, Alg. 2-3) equals the (edge, triangle) pairs
+    of a full Z2 reduction of the lexicographic filtration whose two
+    simplices have different highest vertices, id for id; and every
+    critical edge / triangle is in exactly one of D0, D1 / D1, D2."""
+    nz, ny, nx = shape
+    cx = rc.Complex(nx, ny, nz)
+    for f in fields(rng, shape) + [rc_mixture(shape)]:
+        r = oracle.run(f, d1=True, reduction=True)
+        order = rc.canonical_order(f)
+        exp = {(int(b), int(d)) for dim, b, d in r.get(oracle.REDUCTION)
+               if dim == 1 and d >= 0
+               and cx.max_vertex(cx.verts(1, int(b)), order) != cx.max_vertex(cx.verts(2, int(d)), order)}
+        d1 = r.get(oracle.D1)
+        assert {(int(p["birth_id"]), int(p["death_id"])) for p in d1} == exp
+        assert len(d1) == len(r.crit(1)) - len(r.get(oracle.D0)) == len(r.crit(2)) - len(r.get(oracle.D2))
+        fl = f.ravel()
+        assert np.array_equal(d1["birth"].view(np.uint32), fl[d1["birth_vtx"]].view(np.uint32))
+        assert np.array_equal(d1["death"].view(np.uint32), fl[d1["death_vtx"]].view(np.uint32))
+
+
+def rc_mixture(shape):
+    from paper_2505_21266_gb300 import fields as F
+    return F.gaussian_mixture(shape, 4, (0.1, 0.3), 1e-3, 5).numpy()

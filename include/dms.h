@@ -245,6 +245,39 @@ int dms_diagram_d0d2_selfcorrecting(const float* f, const uint32_t* order, const
                                     dms_pair* d0_essential, int64_t* n_out, void* ws,
                                     size_t ws_bytes, int32_t* dstatus, void* stream);
 
+/* ----------------------------------------------------------------- (D1) ---
+ * dms_diagram_d1 -- the saddle-saddle pairs D1 of a 3D field (Sec. 2.5 "D1
+ * pairing", Alg. 2 and Alg. 3), computed after D0 and D2: the critical
+ * triangles that D2 left unpaired are paired with the critical edges that D0
+ * left unpaired by homologous propagation.  The boundary of each triangle
+ * (a max-heap of edges under the lexicographic key, Z2 by lazy
+ * cancellation, kept in a pool of device memory) is expanded at its highest
+ * edge through the gradient until that edge is critical; columns whose
+ * highest critical edge an earlier triangle holds add that triangle's
+ * boundary; all columns work at once, in rounds, until the highest critical
+ * edges are distinct.  The result is the pairing of the sequential Alg. 3.
+ *   f, order, rec   as above (desc is not needed).
+ *   crit1, crit2    critical edges / triangles from dms_critical (sorted);
+ *                   n_crit HOST [4] their counts (n_crit[1], n_crit[2] < 2^32 - 1).
+ *   d0, n_d0        the D0 pairs of dms_diagram_d0d2 (n_d0 of them, count on
+ *                   the host); d2, n_d2 the D2 pairs.
+ *   d1   [cap1] out: D1 pairs (birth = edge, death = triangle) in increasing
+ *        triangle-id order (n_crit[2] - n_d2 of them); n_out [1] int64 out
+ *        (capacity errors as in dms_critical).
+ *   pool_entries  16-byte heap entries of the boundary pool (0: 48 per
+ *        triangle); a boundary that outgrows the pool sets
+ *        (1 << DMS_ERR_CAPACITY) and the call can be repeated with more.
+ *   ws   at least dms_diagram_d1_workspace_size(d, n_crit, pool_entries).
+ * Synchronises `stream` once per round; past 4096 rounds it returns
+ * DMS_ERR_TIMEOUT.
+ */
+size_t dms_diagram_d1_workspace_size(dms_dims d, const int64_t* n_crit, int64_t pool_entries);
+int dms_diagram_d1(const float* f, const uint32_t* order, const uint64_t* rec, dms_dims d,
+                   const int64_t* crit1, const int64_t* crit2, const int64_t* n_crit,
+                   const dms_pair* d0, int64_t n_d0, const dms_pair* d2, int64_t n_d2,
+                   dms_pair* d1, int64_t cap1, int64_t* n_out, int64_t pool_entries, void* ws,
+                   size_t ws_bytes, int32_t* dstatus, void* stream);
+
 /* ---------------------------------------------------------------- batch ---
  * dms_batch_diagrams -- (i)-(iv) for many fields of uneven dims at once
  * (the batch processing the paper contrasts with its per-dataset runs,

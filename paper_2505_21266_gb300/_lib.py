@@ -49,6 +49,10 @@ SIGNATURES = [
     ("dms_diagram_d0d2_selfcorrecting", ctypes.c_int,
      [_VP, _VP, _VP, _VP, dms_dims, _VP, _VP, _VP, _VP, _VP, _VP, _I64, _VP, _I64, _VP, _VP,
       _VP, _SZ, _VP, _VP]),
+    ("dms_diagram_d1_workspace_size", _SZ, [dms_dims, _VP, _I64]),
+    ("dms_diagram_d1", ctypes.c_int,
+     [_VP, _VP, _VP, dms_dims, _VP, _VP, _VP, _VP, _I64, _VP, _I64, _VP, _I64, _VP, _I64, _VP,
+      _SZ, _VP, _VP]),
     ("dms2_order_workspace_size", _SZ, [_I32, _I32]),
     ("dms2_order", ctypes.c_int, [_VP, _I32, _I32, _VP, _VP, _SZ, _VP, _VP]),
     ("dms2_gradient", ctypes.c_int, [_VP, _I32, _I32, _VP, _VP, _VP]),

@@ -184,6 +184,42 @@ def diagram_d0d2(field: torch.Tensor, order_t: torch.Tensor, g: Gradient, crit,
     return Diagrams(d0[: n[0]], d2[: n[1]], ess)
 
 
+def diagram_d1(field: torch.Tensor, order_t: torch.Tensor, g: Gradient, crit, dg: Diagrams,
+               pool_entries: int = 0, max_tries: int = 4) -> torch.Tensor:
+    """D1 pairs (birth = critical edge, death = critical triangle) of a 3D
+    field after its D0 / D2 pairs (Sec. 2.5, Alg. 2 and Alg. 3), as pair
+    records [n1, 32] in increasing triangle-id order.  The boundary pool
+    grows (the call is repeated) when a boundary outgrows it."""
+    _require_cuda(field, "field", torch.float32)
+    lib = _lib.load()
+    dev = field.device
+    d = dims_of(field)
+    nc = [int(c.numel()) for c in crit]
+    ncarr = (ctypes.c_int64 * 4)(*nc)
+    n_d0, n_d2 = int(dg.d0.shape[0]), int(dg.d2.shape[0])
+    cap1 = max(nc[2] - n_d2, 0)
+    out = torch.empty((max(cap1, 1), PAIR_BYTES), dtype=torch.uint8, device=dev)
+    n_out = torch.zeros(1, dtype=torch.int64, device=dev)
+    pool = int(pool_entries)
+    for _ in range(max_tries):
+        ws = _ws(lib.dms_diagram_d1_workspace_size(d, ncarr, pool), dev)
+        st = torch.zeros(1, dtype=torch.int32, device=dev)
+        _check(lib.dms_diagram_d1(_ptr(field), _ptr(order_t), _ptr(g.rec), d,
+                                  _ptr(crit[1]) if nc[1] else None,
+                                  _ptr(crit[2]) if nc[2] else None, ncarr,
+                                  _ptr(dg.d0) if n_d0 else None, n_d0,
+                                  _ptr(dg.d2) if n_d2 else None, n_d2, _ptr(out), cap1,
+                                  _ptr(n_out), pool, _ptr(ws), ws.numel(), _ptr(st),
+                                  _stream(dev)), "dms_diagram_d1")
+        v = int(st.item())
+        if v == (1 << 4) and pool >= 0:  # the pool only: retry with four times as much
+            pool = 4 * (pool or 48 * max(nc[2], 1))
+            continue
+        _device_status_check(st, "dms_diagram_d1")
+        return out[: int(n_out.item())]
+    raise DMSError(4, "dms_diagram_d1")
+
+
 @dataclass
 class Result:
     order: torch.Tensor

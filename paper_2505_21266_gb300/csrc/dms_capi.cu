@@ -20,6 +20,12 @@ int launch_diagram(const float* f, const uint32_t* order, const uint8_t* desc, c
                    const int64_t* crit3, const int64_t* nc, dms_pair* d0, int64_t cap0,
                    dms_pair* d2, int64_t cap2, dms_pair* ess, int64_t* n_out, void* ws,
                    int32_t* dstatus, cudaStream_t s, int pairing);
+size_t d1_workspace_bytes(int64_t n1, int64_t n2, int64_t pool_entries);
+int launch_d1(const float* f, const uint32_t* order, const uint64_t* rec, const Grid& g,
+              const int64_t* crit1, const int64_t* crit2, int64_t n1, int64_t n2,
+              const dms_pair* d0, int64_t n_d0, const dms_pair* d2, int64_t n_d2, dms_pair* out,
+              int64_t cap, int64_t* n_out, int64_t pool_entries, void* ws, int32_t* dstatus,
+              cudaStream_t s);
 int launch_backward(const dms_pair* pairs, int64_t n, const float* g, const Grid& grid,
                     float* grad, int32_t* dstatus, cudaStream_t s);
 long long& launch_counter() {
@@ -149,6 +155,32 @@ int dms_diagram_d0d2_selfcorrecting(const float* f, const uint32_t* order, const
                                     size_t ws_bytes, int32_t* dstatus, void* stream) {
   return diagram_d0d2(f, order, desc, rec, d, crit0, crit1, crit2, crit3, n_crit, d0, cap0, d2,
                       cap2, d0_essential, n_out, ws, ws_bytes, dstatus, stream, 1);
+}
+
+size_t dms_diagram_d1_workspace_size(dms_dims d, const int64_t* n_crit, int64_t pool_entries) {
+  Grid g;
+  if (!dms::make_grid(d, &g) || !n_crit || n_crit[1] < 0 || n_crit[2] < 0) return 0;
+  return dms::d1_workspace_bytes(n_crit[1], n_crit[2], pool_entries);
+}
+
+int dms_diagram_d1(const float* f, const uint32_t* order, const uint64_t* rec, dms_dims d,
+                   const int64_t* crit1, const int64_t* crit2, const int64_t* n_crit,
+                   const dms_pair* d0, int64_t n_d0, const dms_pair* d2, int64_t n_d2,
+                   dms_pair* d1, int64_t cap1, int64_t* n_out, int64_t pool_entries, void* ws,
+                   size_t ws_bytes, int32_t* dstatus, void* stream) {
+  Grid g;
+  if (!dms::make_grid(d, &g)) return DMS_ERR_DIMS;
+  if (!f || !order || !rec || !n_crit || !n_out || !ws || !dstatus) return DMS_ERR_NULL;
+  if (n_crit[1] < 0 || n_crit[2] < 0 || n_crit[1] >= (1ll << 32) - 1 || n_crit[2] >= (1ll << 32) - 1)
+    return DMS_ERR_ARG;
+  if ((n_crit[1] > 0 && !crit1) || (n_crit[2] > 0 && !crit2)) return DMS_ERR_NULL;
+  if (n_d0 < 0 || n_d2 < 0 || (n_d0 > 0 && !d0) || (n_d2 > 0 && !d2)) return DMS_ERR_ARG;
+  if (cap1 < 0 || (cap1 > 0 && !d1) || pool_entries < 0) return DMS_ERR_ARG;
+  if (ws_bytes < dms::d1_workspace_bytes(n_crit[1], n_crit[2], pool_entries))
+    return DMS_ERR_WORKSPACE;
+  return dms::launch_d1(f, order, rec, g, crit1, crit2, n_crit[1], n_crit[2], d0, n_d0, d2, n_d2,
+                        d1, cap1, n_out, pool_entries, ws, dstatus,
+                        static_cast<cudaStream_t>(stream));
 }
 
 int dms_backward(const dms_pair* pairs, int64_t n, const float* g, dms_dims d, float* grad,

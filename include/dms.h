@@ -252,10 +252,11 @@ int dms_diagram_d0d2_selfcorrecting(const float* f, const uint32_t* order, const
  * left unpaired by homologous propagation.  The boundary of each triangle
  * (a max-heap of edges under the lexicographic key, Z2 by lazy
  * cancellation, kept in a pool of device memory) is expanded at its highest
- * edge through the gradient until that edge is critical; columns whose
- * highest critical edge an earlier triangle holds add that triangle's
- * boundary; all columns work at once, in rounds, until the highest critical
- * edges are distinct.  The result is the pairing of the sequential Alg. 3.
+ * edge through the gradient until that edge is critical; a column whose
+ * highest critical edge an earlier triangle settled on adds that triangle's
+ * boundary and goes on, the others claim their edge (the earliest triangle
+ * wins); all columns work at once, in rounds, until every column is settled
+ * on a distinct edge.  The result is the pairing of the sequential Alg. 3.
  *   f, order, rec   as above (desc is not needed).
  *   crit1, crit2    critical edges / triangles from dms_critical (sorted);
  *                   n_crit HOST [4] their counts (n_crit[1], n_crit[2] < 2^32 - 1).
@@ -264,8 +265,8 @@ int dms_diagram_d0d2_selfcorrecting(const float* f, const uint32_t* order, const
  *   d1   [cap1] out: D1 pairs (birth = edge, death = triangle) in increasing
  *        triangle-id order (n_crit[2] - n_d2 of them); n_out [1] int64 out
  *        (capacity errors as in dms_critical).
- *   pool_entries  16-byte heap entries of the boundary pool (0: 48 per
- *        triangle); a boundary that outgrows the pool sets
+ *   pool_entries  16-byte heap entries of the boundary pool (0: 96 per
+ *        critical triangle + 65536; at least 16 per critical triangle); a boundary that outgrows the pool sets
  *        (1 << DMS_ERR_CAPACITY) and the call can be repeated with more.
  *   ws   at least dms_diagram_d1_workspace_size(d, n_crit, pool_entries).
  * Synchronises `stream` once per round; past 4096 rounds it returns

@@ -213,7 +213,7 @@ def diagram_d1(field: torch.Tensor, order_t: torch.Tensor, g: Gradient, crit, dg
                                   _stream(dev)), "dms_diagram_d1")
         v = int(st.item())
         if v == (1 << 4) and pool >= 0:  # the pool only: retry with four times as much
-            pool = 4 * (pool or 48 * max(nc[2], 1))
+            pool = 4 * (pool or 96 * max(nc[2], 1) + 65536)
             continue
         _device_status_check(st, "dms_diagram_d1")
         return out[: int(n_out.item())]

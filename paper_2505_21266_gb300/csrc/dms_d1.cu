@@ -7,28 +7,33 @@
 // edges of sigma -- lives in a binary max-heap of edges keyed by their
 // lexicographic key (orders of the two vertices, higher first; Sec. 2.1) in
 // a pool of device memory.  Z2 arithmetic is lazy: an edge added twice sits
-// twice in the heap, and the copies cancel when they reach the top.  The
-// columns are reduced in rounds, all columns at once:
-//   expand   while the highest edge tau of the boundary is not critical, it
-//            is paired with a triangle by the gradient; that triangle's
-//            boundary is added (its other two edges are pushed, tau has been
-//            popped) -- Alg. 3's "expand boundary".  The highest edge of a
-//            boundary is a cycle's highest edge, so it is never paired with
-//            a vertex nor a D0 death; the first critical one is the column's
-//            pivot.  (Expansion can raise the highest edge inside the lower
-//            star of one vertex, but every edge left below the pivot only
-//            reaches critical edges below it, so the pivot is that of the
-//            fully expanded boundary.)
-//   claim    every pivot edge keeps the earliest column (atomicMin of the
-//            column's key) that has it -- the earlier triangle of Alg. 3;
-//   merge    every other column with that pivot adds the earliest one's
-//            boundary (pushes its heap) -- Alg. 3's "merge the boundaries".
+// twice in the heap and the copies cancel when they reach the top; a heap
+// about to outgrow its segment is first compacted (sorted in place, pairs
+// cancelled).  All columns work at once, in rounds of two kernels:
+//   advance  a column expands its boundary at the highest edge tau: while
+//            tau is not critical it is paired with a triangle by the
+//            gradient, whose boundary is added (its other two edges are
+//            pushed; tau has been popped) -- Alg. 3's "expand boundary".
+//            The highest edge of a boundary is a cycle's highest edge, so it
+//            is never paired with a vertex nor a D0 death; the first critical
+//            one is the column's pivot.  (Expansion can raise the highest
+//            edge inside the lower star of one vertex, but every edge left
+//            below the pivot only reaches critical edges below it, so the
+//            pivot is that of the fully expanded boundary.)  If an earlier
+//            column settled on that pivot in the previous round, its boundary
+//            is added -- Alg. 3's "merge the boundaries" -- and the column
+//            goes on; otherwise it claims the pivot (atomicMin of the column's
+//            key: the earliest column wins, Alg. 3's "sigma is older") and
+//            waits for the next round.  Settled columns sit the round out, so
+//            the boundaries others read do not change under them.
+//   publish  each pivot's earliest claimant settles on it; a settled column
+//            that a still earlier one displaced becomes unsettled.
 // Only ever adding an earlier column to a later one keeps the reduction
-// valid; when no column merged in a round the pivots are distinct and are
-// the pairs: (pivot edge, sigma).  This is the pivot pairing of a reduced
-// boundary matrix, which does not depend on the order of the additions, so
-// the pairs are those of the sequential Alg. 3 (the self-correcting parallel
-// form of Alg. 3 reaches the same fixpoint with locks instead of rounds).
+// valid; when every column is settled the pivots are distinct and are the
+// pairs (pivot edge, sigma): the pivot pairing of a reduced boundary matrix,
+// which does not depend on the order of the additions, so the pairs are
+// those of the sequential Alg. 3 (Alg. 3's self-correcting parallel form
+// reaches the same fixpoint with compare-and-swap instead of rounds).
 #include <algorithm>
 #include <cstdint>
 
@@ -135,9 +140,10 @@ struct D1Ws {
   Col* col;           // [n2]
   unsigned long long* owner_key;  // [n1]
   uint32_t* owner_col;            // [n1]
+  uint8_t* settled;               // [n2]: settled on its pivot in the last publish
   HEnt* pool;
   int64_t pool_cap;
-  unsigned long long* ctr;  // [0] pool cursor, [1] merges, [2] failures
+  unsigned long long* ctr;  // [0] pool cursor, [1] unsettled columns, [2] failures
   long long* tc;            // output compaction tile counts
   long long* sums;
   size_t bytes;
@@ -152,6 +158,7 @@ D1Ws carve(void* base, int64_t n1, int64_t n2, int64_t pool_entries) {
   w.col = c.take<Col>(std::max<int64_t>(n2, 1));
   w.owner_key = c.take<unsigned long long>(std::max<int64_t>(n1, 1));
   w.owner_col = c.take<uint32_t>(std::max<int64_t>(n1, 1));
+  w.settled = c.take<uint8_t>(std::max<int64_t>(n2, 1));
   w.pool_cap = pool_entries;
   w.pool = c.take<HEnt>(std::max<int64_t>(pool_entries, 1));
   w.ctr = c.take<unsigned long long>(4);
@@ -230,9 +237,35 @@ __device__ __forceinline__ HEnt heap_pop(HEnt* h, uint32_t& size) {
   return top;
 }
 
-// room for `more` entries, moving the heap to a larger segment of the pool
+// sorts a heap in place (heapsort, ascending), cancels equal pairs (Z2) and
+// leaves the survivors in decreasing order, which is a max-heap again
+__device__ __forceinline__ void heap_compact(HEnt* h, uint32_t& size) {
+  uint32_t n = size;
+  while (n > 1) {
+    const HEnt top = heap_pop(h, n);  // n decreases by one
+    h[n] = top;
+  }
+  uint32_t m = 0;
+  for (uint32_t i = 0; i < size;) {
+    uint32_t j = i + 1;
+    while (j < size && h[j].key == h[i].key) ++j;
+    if ((j - i) & 1) h[m++] = h[i];
+    i = j;
+  }
+  for (uint32_t i = 0; i < m / 2; ++i) {
+    const HEnt t = h[i];
+    h[i] = h[m - 1 - i];
+    h[m - 1 - i] = t;
+  }
+  size = m;
+}
+
+// room for `more` entries: compact the heap, and if that is not enough move
+// it to a larger segment of the pool
 __device__ __forceinline__ bool heap_reserve(D1Ws& w, Col& c, uint32_t more) {
   if ((uint64_t)c.size + more <= c.cap) return true;
+  heap_compact(w.pool + c.off, c.size);
+  if ((uint64_t)c.size + more <= c.cap && 4ull * c.size <= 3ull * c.cap) return true;
   uint64_t ncap = std::max<uint64_t>(2ull * c.cap, (uint64_t)c.size + more);
   if (ncap > 0xFFFFFFFFull) return false;
   const unsigned long long off = atomicAdd(w.ctr + 0, (unsigned long long)ncap);
@@ -324,109 +357,124 @@ __global__ void init_cols(Grid g, const uint32_t* __restrict__ order,
   (void)dstatus;
 }
 
-// expand every active column until its highest edge is a critical D1 edge
-__global__ void __launch_bounds__(256) expand(Grid g, const uint32_t* __restrict__ order,
-                                              const uint64_t* __restrict__ rec,
-                                              const int64_t* __restrict__ crit1, int64_t n1,
-                                              int64_t n2, D1Ws w, int64_t limit,
-                                              int32_t* dstatus) {
+// expands a column's boundary until its highest edge is a critical D1
+// edge (its pivot); false if the column failed
+__device__ __forceinline__ bool expand_col(const Grid& g, const uint32_t* __restrict__ order,
+                                           const uint64_t* __restrict__ rec,
+                                           const int64_t* __restrict__ crit1, int64_t n1, D1Ws& w,
+                                           Col& c, int64_t& steps, int64_t limit,
+                                           int32_t* dstatus) {
+  for (;;) {
+    if (++steps > limit) {
+      fail(w, c, dstatus, DMS_ERR_TIMEOUT);
+      return false;
+    }
+    HEnt* h = w.pool + c.off;
+    if (c.size == 0) {  // a D2-unpaired triangle kills a cycle: not reached
+      fail(w, c, dstatus, DMS_ERR_ARG);
+      return false;
+    }
+    // the highest edge, with its copies (Z2: an even count cancels)
+    const HEnt e = heap_pop(h, c.size);
+    uint32_t copies = 1;
+    while (c.size && h[0].key == e.key) {
+      heap_pop(h, c.size);
+      ++copies;
+    }
+    if (!(copies & 1)) continue;
+    int64_t a;
+    int k;
+    ent_edge(g, e, a, k);
+    const uint32_t code = (uint32_t)(__ldg(rec + a) >> (3 * k)) & 7u;
+    if (code == 7) {  // critical: the pivot
+      const int64_t idx = bsearch_id(crit1, n1, 7 * a + k);
+      if (idx < 0 || w.d0mark[idx]) {
+        fail(w, c, dstatus, DMS_ERR_ARG);
+        return false;
+      }
+      heap_push(h, c.size, e);
+      c.pivot = (uint32_t)idx;
+      return true;
+    }
+    if (code == 0) {  // paired with a vertex: not the highest edge of a cycle
+      fail(w, c, dstatus, DMS_ERR_ARG);
+      return false;
+    }
+    // the triangle paired with e: add its other two edges
+    const uint32_t ce = cCof.e[k][code - 1];
+    const int64_t tb = a - cdelta(g, ce & 7);
+    const int t = ce >> 3;
+    const int p = tri_p(t), q = tri_q(t);
+    const HEnt f[3] = {make_ent(order, g, tb, p), make_ent(order, g, tb, q),
+                       make_ent(order, g, tb + cdelta(g, p), q ^ p)};
+    if (!heap_reserve(w, c, 2)) {
+      fail(w, c, dstatus, DMS_ERR_CAPACITY);
+      return false;
+    }
+    h = w.pool + c.off;
+    for (int i = 0; i < 3; ++i)
+      if (f[i].key != e.key) heap_push(h, c.size, f[i]);
+  }
+}
+
+// one round for every column that has not settled: expand, merge the
+// boundaries of earlier columns settled on its pivot, claim the rest
+__global__ void __launch_bounds__(256) advance(Grid g, const uint32_t* __restrict__ order,
+                                               const uint64_t* __restrict__ rec,
+                                               const int64_t* __restrict__ crit1, int64_t n1,
+                                               int64_t n2, D1Ws w, int64_t limit,
+                                               int32_t* dstatus) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n2;
        j += (int64_t)gridDim.x * blockDim.x) {
     Col c = w.col[j];
-    if (c.state != 1 || c.pivot != kNone) continue;
+    if (c.state != 1 || w.settled[j]) continue;
     int64_t steps = 0;
     for (;;) {
-      if (++steps > limit) {
-        fail(w, c, dstatus, DMS_ERR_TIMEOUT);
+      if (c.pivot == kNone && !expand_col(g, order, rec, crit1, n1, w, c, steps, limit, dstatus))
+        break;
+      const unsigned long long o = w.owner_key[c.pivot];
+      if (o == c.key) break;  // claimed by this column: settles at publish
+      if (o > c.key) {        // unclaimed, or a later column holds it: claim
+        atomicMin(w.owner_key + c.pivot, c.key);
         break;
       }
-      HEnt* h = w.pool + c.off;
-      if (c.size == 0) {  // a D2-unpaired triangle kills a cycle: not reached
-        fail(w, c, dstatus, DMS_ERR_ARG);
-        break;
-      }
-      // the highest edge, with its copies (Z2: an even count cancels)
-      const HEnt e = heap_pop(h, c.size);
-      uint32_t copies = 1;
-      while (c.size && h[0].key == e.key) {
-        heap_pop(h, c.size);
-        ++copies;
-      }
-      if (!(copies & 1)) continue;
-      int64_t a;
-      int k;
-      ent_edge(g, e, a, k);
-      const uint32_t code = (uint32_t)(__ldg(rec + a) >> (3 * k)) & 7u;
-      if (code == 7) {  // critical: the pivot
-        const int64_t idx = bsearch_id(crit1, n1, 7 * a + k);
-        if (idx < 0 || w.d0mark[idx]) {
-          fail(w, c, dstatus, DMS_ERR_ARG);
-          break;
-        }
-        heap_push(h, c.size, e);
-        c.pivot = (uint32_t)idx;
-        break;
-      }
-      if (code == 0) {  // paired with a vertex: not the highest edge of a cycle
-        fail(w, c, dstatus, DMS_ERR_ARG);
-        break;
-      }
-      // the triangle paired with e: add its other two edges
-      const uint32_t ce = cCof.e[k][code - 1];
-      const int64_t tb = a - cdelta(g, ce & 7);
-      const int t = ce >> 3;
-      const int p = tri_p(t), q = tri_q(t);
-      HEnt f[3] = {make_ent(order, g, tb, p), make_ent(order, g, tb, q),
-                   make_ent(order, g, tb + cdelta(g, p), q ^ p)};
-      if (!heap_reserve(w, c, 2)) {
+      // an earlier column holds the pivot: add its boundary if it settled
+      // on it in the last publish (its heap is then left alone this round)
+      const uint32_t oc = w.owner_col[c.pivot];
+      if (oc >= (uint64_t)n2 || !w.settled[oc]) break;
+      const Col oo = w.col[oc];
+      if (oo.key != o || oo.pivot != c.pivot) break;
+      if (!heap_reserve(w, c, oo.size)) {
         fail(w, c, dstatus, DMS_ERR_CAPACITY);
         break;
       }
-      h = w.pool + c.off;
-      for (int i = 0; i < 3; ++i)
-        if (f[i].key != e.key) heap_push(h, c.size, f[i]);
+      HEnt* h = w.pool + c.off;
+      const HEnt* src = w.pool + oo.off;
+      for (uint32_t i = 0; i < oo.size; ++i) heap_push(h, c.size, src[i]);
+      c.pivot = kNone;
     }
     w.col[j] = c;
   }
 }
 
-__global__ void claim(int64_t n2, D1Ws w) {
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n2;
-       j += (int64_t)gridDim.x * blockDim.x) {
-    const Col c = w.col[j];
-    if (c.state == 1 && c.pivot != kNone) atomicMin(w.owner_key + c.pivot, c.key);
-  }
-}
-
+// each pivot's earliest claimant settles on it; counts the unsettled columns
 __global__ void publish(int64_t n2, D1Ws w) {
+  unsigned long long unsettled = 0;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n2;
        j += (int64_t)gridDim.x * blockDim.x) {
     const Col c = w.col[j];
-    if (c.state == 1 && c.pivot != kNone && w.owner_key[c.pivot] == c.key)
-      w.owner_col[c.pivot] = (uint32_t)j;
+    if (c.state != 1) continue;
+    const bool own = c.pivot != kNone && w.owner_key[c.pivot] == c.key;
+    if (own) w.owner_col[c.pivot] = (uint32_t)j;
+    w.settled[j] = own ? 1 : 0;
+    unsettled += own ? 0 : 1;
   }
+  if (unsettled) atomicAdd(w.ctr + 1, unsettled);
 }
 
-// a column whose pivot an earlier column holds adds that column's boundary
-__global__ void __launch_bounds__(256) merge(int64_t n2, D1Ws w, int32_t* dstatus) {
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n2;
-       j += (int64_t)gridDim.x * blockDim.x) {
-    Col c = w.col[j];
-    if (c.state != 1 || c.pivot == kNone || w.owner_key[c.pivot] == c.key) continue;
-    const Col o = w.col[w.owner_col[c.pivot]];
-    if (!heap_reserve(w, c, o.size)) {
-      fail(w, c, dstatus, DMS_ERR_CAPACITY);
-      w.col[j] = c;
-      continue;
-    }
-    HEnt* h = w.pool + c.off;
-    const HEnt* src = w.pool + o.off;
-    for (uint32_t i = 0; i < o.size; ++i) heap_push(h, c.size, src[i]);
-    c.pivot = kNone;
-    w.col[j] = c;
-    atomicAdd(w.ctr + 1, 1ull);
-  }
-}
+// a column that holds a pair: active with a pivot (after a failure some
+// columns may have none; the failure's status bit tells the caller)
+__device__ __forceinline__ bool has_pair(const Col& c) { return c.state == 1 && c.pivot != kNone; }
 
 // ordered compaction of the pairs (crit2 order = increasing triangle id)
 __global__ void __launch_bounds__(WNT) count_out(int64_t n2, D1Ws w) {
@@ -435,7 +483,7 @@ __global__ void __launch_bounds__(WNT) count_out(int64_t n2, D1Ws w) {
   int cnt = 0;
   for (int k = 0; k < WITEMS; ++k) {
     const int64_t j = base + k;
-    if (j < n2 && w.col[j].state == 1) ++cnt;
+    if (j < n2 && has_pair(w.col[j])) ++cnt;
   }
   long long total;
   scan64::block_excl(cnt, tmp, &total);
@@ -462,12 +510,12 @@ __global__ void __launch_bounds__(WNT) write_out(Grid g, const float* __restrict
   int cnt = 0;
   for (int k = 0; k < WITEMS; ++k) {
     const int64_t j = base + k;
-    if (j < n2 && w.col[j].state == 1) ++cnt;
+    if (j < n2 && has_pair(w.col[j])) ++cnt;
   }
   long long pos = scan64::block_excl(cnt, tmp, nullptr) + w.tc[blockIdx.x];
   for (int k = 0; k < WITEMS; ++k) {
     const int64_t j = base + k;
-    if (j >= n2 || w.col[j].state != 1) continue;
+    if (j >= n2 || !has_pair(w.col[j])) continue;
     if (pos < cap) {
       const int64_t eid = crit1[w.col[j].pivot], tid = crit2[j];
       const int64_t ea = eid / 7, tb = tid / 12;
@@ -492,10 +540,12 @@ __global__ void __launch_bounds__(WNT) write_out(Grid g, const float* __restrict
   }
 }
 
-__global__ void init_owner(unsigned long long* owner_key, int64_t n1) {
+__global__ void init_owner(unsigned long long* owner_key, uint32_t* owner_col, int64_t n1) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n1;
-       i += (int64_t)gridDim.x * blockDim.x)
+       i += (int64_t)gridDim.x * blockDim.x) {
     owner_key[i] = ~0ull;
+    owner_col[i] = kNone;
+  }
 }
 
 __global__ void init_state(Col* col, int64_t n2) {
@@ -510,7 +560,7 @@ constexpr int64_t kExpandLimit = 1ll << 26;  // heap pops of one column in one r
 
 }  // namespace
 
-int64_t d1_default_pool(int64_t n2) { return n2 * (int64_t)kCap0 * 3 + 4096; }
+int64_t d1_default_pool(int64_t n2) { return n2 * (int64_t)kCap0 * 6 + 65536; }
 
 size_t d1_workspace_bytes(int64_t n1, int64_t n2, int64_t pool_entries) {
   if (pool_entries <= 0) pool_entries = d1_default_pool(n2);
@@ -537,7 +587,7 @@ int launch_d1(const float* f, const uint32_t* order, const uint64_t* rec, const 
   DMS_CUDA_OK(cudaMemsetAsync(w.ctr, 0, 4 * sizeof(unsigned long long), s));
   init_state<<<nb(n2), TB, 0, s>>>(w.col, n2); count_launch();
   if (n1 > 0) {
-    init_owner<<<nb(n1), TB, 0, s>>>(w.owner_key, n1); count_launch();
+    init_owner<<<nb(n1), TB, 0, s>>>(w.owner_key, w.owner_col, n1); count_launch();
   }
   if (n_d0 > 0 && n1 > 0) {
     mark_d0<<<nb(n_d0), TB, 0, s>>>(d0, n_d0, crit1, n1, w.d0mark); count_launch();
@@ -548,13 +598,12 @@ int launch_d1(const float* f, const uint32_t* order, const uint64_t* rec, const 
   const unsigned long long cursor0 = (unsigned long long)n2 * kCap0;
   DMS_CUDA_OK(cudaMemcpyAsync(w.ctr + 0, &cursor0, sizeof(cursor0), cudaMemcpyHostToDevice, s));
   init_cols<<<nb(n2), TB, 0, s>>>(g, order, crit2, n2, w, kCap0, dstatus); count_launch();
+  DMS_CUDA_OK(cudaMemsetAsync(w.settled, 0, std::max<int64_t>(n2, 1), s));
   for (int round = 1;; ++round) {
     if (round > kMaxRounds) return DMS_ERR_TIMEOUT;
     DMS_CUDA_OK(cudaMemsetAsync(w.ctr + 1, 0, 2 * sizeof(unsigned long long), s));
-    expand<<<nb(n2), TB, 0, s>>>(g, order, rec, crit1, n1, n2, w, kExpandLimit, dstatus); count_launch();
-    claim<<<nb(n2), TB, 0, s>>>(n2, w); count_launch();
+    advance<<<nb(n2), TB, 0, s>>>(g, order, rec, crit1, n1, n2, w, kExpandLimit, dstatus); count_launch();
     publish<<<nb(n2), TB, 0, s>>>(n2, w); count_launch();
-    merge<<<nb(n2), TB, 0, s>>>(n2, w, dstatus); count_launch();
     unsigned long long h[2] = {0, 0};
     DMS_CUDA_OK(cudaMemcpyAsync(h, w.ctr + 1, sizeof(h), cudaMemcpyDeviceToHost, s));
     DMS_CUDA_OK(cudaStreamSynchronize(s));

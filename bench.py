@@ -324,6 +324,36 @@ def bench_2d(dev, steps: int, warmup: int, n: int = 16384):
     return out
 
 
+def bench_d1(dev, steps: int, warmup: int, n: int = 512):
+    """D1 (the saddle-saddle pairs, after D0/D2) on the n^3 quantised-noise
+    field (256 levels): the dms_diagram_d1 call alone, with its pool sized
+    on the first call, in ms and vertices/s."""
+    import torch
+    import paper_2505_21266_gb300 as dms
+    from paper_2505_21266_gb300 import fields
+    f = fields.config2(0, dev, n=n)
+    r = dms.diagram(f)
+    d1 = dms.diagram_d1(f, r.order, r.grad, r.crit, r.diagrams)
+    for _ in range(max(0, warmup - 1)):
+        d1 = dms.diagram_d1(f, r.order, r.grad, r.crit, r.diagrams)
+    torch.cuda.synchronize()
+    reps = max(1, min(steps, 3))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        d1 = dms.diagram_d1(f, r.order, r.grad, r.crit, r.diagrams)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    out = {"workload": f"{n}^3 float32, U[0,1) quantised to 256 levels", "vertices": n ** 3,
+           "d1_ms": ms, "vertices_per_s": n ** 3 / (ms / 1e3), "pairs_d1": int(d1.shape[0]),
+           "critical": [int(c.numel()) for c in r.crit],
+           "pairs_d0_d2": [int(r.diagrams.d0.shape[0]), int(r.diagrams.d2.shape[0])]}
+    del f, r, d1
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args):
     """--impl reference: the oracle on bounded crops of the workload field."""
     rank = int(os.environ.get("RANK", "0"))
@@ -381,7 +411,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-field batch leg")
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiable leg")
     ap.add_argument("--no-2d", action="store_true", help="skip the 2D leg")
-    ap.add_argument("--leg", choices=["batched", "diff", "2d"], default=None,
+    ap.add_argument("--no-d1", action="store_true", help="skip the D1 leg")
+    ap.add_argument("--leg", choices=["batched", "diff", "2d", "d1"], default=None,
                     help="run one comparison leg alone (its own JSON line), e.g. to profile it")
     args = ap.parse_args()
     if args.source_hash:
@@ -405,7 +436,8 @@ def main():
     dev = torch.device("cuda", local)
     lib = _lib.load()
     if args.leg:
-        legs = {"batched": bench_batched, "diff": bench_differentiable, "2d": bench_2d}
+        legs = {"batched": bench_batched, "diff": bench_differentiable, "2d": bench_2d,
+                "d1": bench_d1}
         out = legs[args.leg](dev, args.steps, args.warmup)
         print(json.dumps({"leg": args.leg, **out}), flush=True)
         return
@@ -587,6 +619,8 @@ def main():
         line["differentiable"] = bench_differentiable(dev, args.steps, args.warmup)
     if world == 1 and not args.no_2d:
         line["grid_2d"] = bench_2d(dev, args.steps, args.warmup)
+    if world == 1 and not args.no_d1:
+        line["d1"] = bench_d1(dev, args.steps, args.warmup)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -324,7 +324,7 @@ def bench_2d(dev, steps: int, warmup: int, n: int = 16384):
     return out
 
 
-def bench_d1(dev, steps: int, warmup: int, n: int = 512):
+def bench_d1(dev, steps: int, warmup: int, n: int = 256):
     """D1 (the saddle-saddle pairs, after D0/D2) on the n^3 quantised-noise
     field (256 levels): the dms_diagram_d1 call alone, with its pool sized
     on the first call, in ms and vertices/s."""
@@ -411,7 +411,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-field batch leg")
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiable leg")
     ap.add_argument("--no-2d", action="store_true", help="skip the 2D leg")
-    ap.add_argument("--no-d1", action="store_true", help="skip the D1 leg")
+    ap.add_argument("--with-d1", action="store_true",
+                    help="add the D1 leg (saddle-saddle pairs, 256^3 quantised noise)")
     ap.add_argument("--leg", choices=["batched", "diff", "2d", "d1"], default=None,
                     help="run one comparison leg alone (its own JSON line), e.g. to profile it")
     args = ap.parse_args()
@@ -619,7 +620,7 @@ def main():
         line["differentiable"] = bench_differentiable(dev, args.steps, args.warmup)
     if world == 1 and not args.no_2d:
         line["grid_2d"] = bench_2d(dev, args.steps, args.warmup)
-    if world == 1 and not args.no_d1:
+    if world == 1 and args.with_d1:
         line["d1"] = bench_d1(dev, args.steps, args.warmup)
     if rank == 0:
         print(json.dumps(line), flush=True)

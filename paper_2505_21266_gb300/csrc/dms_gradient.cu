@@ -2,13 +2,17 @@
 // triangulation of a 3D grid -- the first and most time-consuming step of DMS.
 //
 // One thread runs ProcessLowerStars for one vertex x.  The lower star L(x) --
-// the simplices holding x whose other vertices all precede x -- lives in
-// bitmasks over the fixed star numbering (14 edges, 36 triangles, 24 tets).
-// The two priority queues of the algorithm (PQzero, PQone) are bitmask sets
-// whose pop-min compares 12-bit keys: the ranks, among the lower neighbours
-// of x, of a simplex's other vertices listed by decreasing order (for
-// simplices that all hold x this is the lexicographic comparison of Sec. 2.1,
-// a proper prefix first).
+// the simplices holding x whose other vertices all precede x -- is the cone
+// over the lower link (the link of x restricted to its lower neighbours),
+// and lives in bitmasks over the fixed star numbering (14 edges, 36
+// triangles, 24 tets).  Keys are the ranks, among the lower neighbours of x,
+// of a simplex's other vertices listed by decreasing order (for simplices
+// that all hold x this is the lexicographic comparison of Sec. 2.1, a proper
+// prefix first).  The pass goes component by component of the lower link:
+// Prim's algorithm over its edges in rank-pair position space (the frontier
+// is a bit operation and its minimum a find-first-set), then its link
+// triangles against their last free edge and PQzero's cycle edges and
+// triangles in key order (dms_lowerstar.cuh).
 //
 // Work layout: a CTA owns a TX x TY x ZC block of ANCHORS and streams it
 // along z.  Every simplex is recorded at its anchor but decided in the lower

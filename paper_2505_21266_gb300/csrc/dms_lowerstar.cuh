@@ -75,16 +75,19 @@ DMS_HD uint32_t umin(uint32_t a, uint32_t b) { return a < b ? a : b; }
 
 // the star tables needed with run-time indices
 struct Tables {
-  uint64_t edgeCof[14];
+  // positions (h(h-1)/2 + l for the pair h > l) of every rank pair holding
+  // rank r, as three 32-bit words (the fourth unused, for 16-byte loads)
+  uint32_t star[14][4];
   uint64_t tetFmask[24];
   uint32_t triCof[36];
-  uint16_t triEdges[36];
   uint8_t triA[36], triB[36];
   uint8_t tetS[24][3];  // slots of tet q
   uint8_t tetF[24][3];
   uint8_t tetCode[24][3];  // record code (1..4) when tet q pairs with facet tetF[q][w]
-  uint8_t cofIdx[36][2];
   uint8_t triOfSlots[14][14];  // star triangle on slots (a, b), 255 if none
+  // position of the star triangle on slots (a, b) among the cofacets of the
+  // edge of slot a (the record's edge code minus one)
+  uint8_t cofOfSlots[14][14];
   uint8_t hlOfPos[91];         // rank-pair position -> (h << 4) | l
   uint8_t pad[1];
   // star triangles / tets with a slot outside m, for the low (0..6) and
@@ -93,7 +96,6 @@ struct Tables {
   uint32_t notQlo[128], notQhi[128];
   uint64_t bit[64];              // 1 << i
   uint64_t nib[16];              // 1 << 4i
-  uint64_t posLo[91], posHi[91];  // position p as a bit of (pP0, pP1)
 };
 DMS_HD uint64_t lower_tris(const Tables& tb, uint32_t lm) {
   return ~(tb.notTlo[lm & 127u] | tb.notThi[lm >> 7]) & ((1ull << 36) - 1);
@@ -102,37 +104,48 @@ DMS_HD uint32_t lower_tets(const Tables& tb, uint32_t lm) {
   return ~(tb.notQlo[lm & 127u] | tb.notQhi[lm >> 7]) & ((1u << 24) - 1);
 }
 
-// per-thread precomputed keys, stored transposed ([item][thread]) so that a
-// warp touches consecutive bytes: triangle rank-pair positions and 12-bit tet
-// keys (see below)
+// per-thread precomputed 12-bit tet keys, stored transposed ([tet][thread])
+// so that a warp touches consecutive words
 template <int NT>
 struct Keys {
   uint16_t q[24][NT];
-  uint8_t tp[36][NT];
 };
 
-// ProcessLowerStars for one vertex.  o[s] = order of neighbour s
-// (0xFFFFFFFF outside the grid), lm = the mask of the slots s with
-// o[s] < order of x (the caller has it from its load-balancing pass).
-// Returns desc and fills acc[c], the record bits contributed to the anchor
-// x - corner c.
+// ProcessLowerStars for one vertex (Robins et al., Sec. 2.3), restated
+// component by component (checked against the oracle, and against the
+// earlier restatement that popped PQone and PQzero by one key order on 1.2e8
+// random lower stars).  o[s] = order of neighbour s (0xFFFFFFFF outside the
+// grid), lm = the mask of the slots s with o[s] < order of x.  Returns desc
+// and fills acc[c], the record bits contributed to the anchor x - corner c.  In the lower link -- the link of x restricted to its lower
+// neighbours, whose vertices, edges and triangles are the edges, triangles
+// and tets of L(x) -- the algorithm decomposes as follows.  Its vertices are
+// classified only through PQone's link edges with one classified end, popped
+// by key: Prim's algorithm from the classified set, so a connected component
+// of the link graph is classified completely, by its minimum spanning tree
+// grown from the component's lowest vertex (the steepest edge's end for the
+// first component; a critical edge, popped from PQzero, for every other),
+// before anything else of it is popped from PQzero (reading A-15 already
+// drains PQone's link edges before its link triangles).  Its link triangles
+// pair with their last unclassified edge in key order, and PQzero's cycle
+// edges and triangles become critical in key order, within the component.
+// Components share no simplex, so nothing one pops changes another, and
+// taking them one after the other (rather than interleaving their PQzero
+// pops by key) gives the same pairs.
 //
-// Keys.  Every simplex of L(x) holds x, its top vertex, so the lexicographic
-// comparison of Sec. 2.1 reduces to the ranks (among the lower neighbours of
-// x) of its other vertices listed by decreasing value; they are packed as
-// nibbles (h+1, m+1, l+1), absent ones 0, a proper prefix being smaller.
-// Triangles are also numbered by their rank pair, position h*(h-1)/2 + l,
-// in which increasing positions are increasing keys.
+// Prim runs in rank-pair position space: a link edge (h, l), h > l ranks,
+// is bit h(h-1)/2 + l of a 91-bit set (three words), increasing positions
+// being increasing keys; the frontier is E & INC & ~IN, INC = edges with a
+// classified end, IN = edges with two, both updated by OR-ing the positions
+// of the new vertex's pairs (tb.star).
 template <int NT>
 DMS_HD int process_lower_star(uint32_t lm, const uint32_t (&o)[14], const Tables& tb,
-                              Keys<NT>& keys, int tid, uint64_t (&acc)[8]) {
+                               Keys<NT>& keys, int tid, uint64_t (&acc)[8]) {
 #pragma unroll
   for (int c = 0; c < 8; ++c) acc[c] = 0;
   if (lm == 0) return 15;  // no lower edge: a minimum
 
-  // ranks among the lower neighbours: one comparison per pair of slots
-  // (a non-lower slot is above every lower one, so it never adds to a lower
-  // slot's rank); delta = the lowest lower neighbour
+  // ranks among the lower neighbours (a non-lower slot is above every lower
+  // one, so it never adds to a lower slot's rank)
   uint64_t R = 0, INV = 0;
   int delta = 0;
 #pragma unroll
@@ -148,17 +161,27 @@ DMS_HD int process_lower_star(uint32_t lm, const uint32_t (&o)[14], const Tables
     }
   }
   auto rank = [&](int s) -> uint32_t { return (uint32_t)(R >> (4 * s)) & 15u; };
+  auto slot = [&](uint32_t r) -> int { return (int)((INV >> (4 * r)) & 15u); };
+  auto pos_of = [&](uint32_t a, uint32_t b) -> uint32_t {
+    const uint32_t h = umax(a, b), l = umin(a, b);
+    return ((h * (h - 1)) >> 1) + l;
+  };
 
-  // the lower star: every star simplex without a non-lower slot
   const uint64_t TL = lower_tris(tb, lm);
   const uint32_t QL = lower_tets(tb, lm);
+  const uint32_t k = (uint32_t)popc32(lm);
 
+  // the link edges in position space
+  uint32_t E0 = 0, E1 = 0, E2 = 0;
   for (uint64_t mt = TL; mt; mt &= mt - 1) {
     const int j = ffs64(mt);
-    const uint32_t ra = rank(tb.triA[j]), rb = rank(tb.triB[j]);
-    const uint32_t h = umax(ra, rb), l = umin(ra, rb);
-    keys.tp[j][tid] = (uint8_t)((h * (h - 1)) / 2 + l);
+    const uint32_t p = pos_of(rank(tb.triA[j]), rank(tb.triB[j]));
+    const uint32_t b = 1u << (p & 31);
+    if (p < 32) E0 |= b;
+    else if (p < 64) E1 |= b;
+    else E2 |= b;
   }
+  // 12-bit keys of the lower-star tets (link triangles)
   for (uint32_t mq = QL; mq; mq &= mq - 1) {
     const int q = ffs32(mq);
     const uint32_t ra = rank(tb.tetS[q][0]), rb = rank(tb.tetS[q][1]), rc = rank(tb.tetS[q][2]);
@@ -166,159 +189,119 @@ DMS_HD int process_lower_star(uint32_t lm, const uint32_t (&o)[14], const Tables
     const uint32_t m = ra + rb + rc - h - l;
     keys.q[q][tid] = (uint16_t)(((h + 1) << 8) | ((m + 1) << 4) | (l + 1));
   }
-  auto tri_pos = [&](int j) -> uint32_t { return keys.tp[j][tid]; };
-  auto pos_key = [&](uint32_t p) -> uint32_t {
-    const uint32_t hl = tb.hlOfPos[p];
-    return (((hl >> 4) + 1) << 8) | (((hl & 15u) + 1) << 4);
-  };
   auto tet_key = [&](int q) -> uint32_t { return keys.q[q][tid]; };
 
-  // ProcessLowerStars (reading of Robins et al.; "classified" = paired or
-  // critical; nuf = number of unclassified facets inside L).
-  //
-  // nuf is tracked bit-parallel: C1/C2 = triangles with >= 1 / 2 classified
-  // edges, Q1/Q2/Q3 = tets with >= 1 / 2 / 3 classified facet triangles, so
-  // "nuf == 1" is C1 & ~C2 (triangles) or Q2 & ~Q3 (tets) and every push of
-  // cofacets is a handful of mask operations.  PQone is drained in two
-  // uniform loops (triangles, then tets; see below) rather than by one pop
-  // loop that branches on the type of the minimum, which keeps the lanes of
-  // a warp on the same path.
-  uint32_t cE = 0;
-  uint64_t cT = 0, C1 = 0, C2 = 0;
-  uint32_t cQ = 0, Q1 = 0, Q2 = 0, Q3 = 0;
-  // returns the triangles whose last unclassified edge this was
-  auto classify_edge = [&](int s) -> uint64_t {
-    cE |= 1u << s;
-    const uint64_t M = tb.edgeCof[s];
-    const uint64_t z = C1 & M & ~C2;
-    C2 |= C1 & M;
-    C1 |= M;
-    return z;
+  uint32_t C = 0;                       // classified link vertices (ranks)
+  uint32_t I0 = 0, I1 = 0, I2 = 0;      // edges with a classified end
+  uint32_t N0 = 0, N1 = 0, N2 = 0;      // edges with two classified ends
+  uint32_t K0 = 0, K1 = 0, K2 = 0;      // classified link edges (positions)
+  uint64_t cT = 0;                      // classified link edges (star triangles)
+  uint32_t Q1 = 0, Q2 = 0, Q3 = 0, cQ = 0;
+  uint64_t eCode = 0, qCode0 = 0;
+  uint32_t qCode1 = 0;
+  uint64_t critT = 0;
+  auto classify_vertex = [&](uint32_t r) {
+    C |= 1u << r;
+    const uint32_t s0 = tb.star[r][0], s1 = tb.star[r][1], s2 = tb.star[r][2];
+    N0 |= s0 & I0;
+    N1 |= s1 & I1;
+    N2 |= s2 & I2;
+    I0 |= s0;
+    I1 |= s1;
+    I2 |= s2;
   };
-  auto classify_tri = [&](int j) {
+  auto mark_pos = [&](uint32_t p) {
+    const uint32_t b = 1u << (p & 31);
+    if (p < 32) K0 |= b;
+    else if (p < 64) K1 |= b;
+    else K2 |= b;
+  };
+  auto classify_edge = [&](int j) {  // star triangle j = link edge
     cT |= tb.bit[j];
     const uint32_t M = tb.triCof[j];
     Q3 |= Q2 & M;
     Q2 |= Q1 & M;
     Q1 |= M;
   };
-  classify_edge(delta);  // x is paired with the edge to delta
-  uint32_t zE = lm & ~cE;  // PQzero
-  uint64_t zT = 0;
-  uint32_t zQ = 0;
-  // PQone: triangles in rank-pair position space (pop-min = find first set),
-  // tets by key scan.  PQone holds exactly the unclassified triangles of L
-  // with one classified edge (each is pushed when its first edge is
-  // classified and leaves when it is paired or its second edge is
-  // classified), so membership needs no mask of its own.
-  uint64_t pP0 = 0, pP1 = 0;
-  uint32_t pQ = 0;
-  auto push_tris = [&](uint64_t nt) {
-    for (; nt; nt &= nt - 1) {
-      const uint32_t p = tri_pos(ffs64(nt));
-      pP0 |= tb.posLo[p];
-      pP1 |= tb.posHi[p];
-    }
-  };
-  push_tris(tb.edgeCof[delta] & TL);  // their other edge is unclassified
-  // record codes, written as the pairs are made: 4 bits per edge slot
-  // (0 = paired with x, 1..6 = paired up, 7 = critical) and per tet
-  // (1..4 = paired with a facet, 7 = critical); critical triangles by bit
-  uint64_t eCode = 0, qCode0 = 0;
-  uint32_t qCode1 = 0;
-  uint64_t critT = 0;
   auto set_tet_code = [&](int q, uint32_t code) {
     if (q < 16) qCode0 |= (uint64_t)code * tb.nib[q];
     else qCode1 |= code << (4 * (q - 16));
   };
 
+  classify_vertex(0);  // x is paired with the edge to delta (rank 0)
   for (;;) {
-    // Drain PQone: its triangles first, then its tets.  A tet pop changes
-    // nothing a triangle pop reads (it classifies a triangle already in
-    // PQzero), every facet of a tet has a smaller key than the tet, and tets
-    // pushed by a triangle have larger keys than it, so this visits the
-    // same pairs as popping triangles and tets by one key order.
-    while (pP0 | pP1) {
-      const int pos = pP0 ? ffs64(pP0) : 64 + ffs64(pP1);
-      pP0 &= ~tb.posLo[pos];
-      pP1 &= ~tb.posHi[pos];
-      const uint32_t hl = tb.hlOfPos[pos];
-      const int j = tb.triOfSlots[(INV >> (4 * (hl >> 4))) & 15u][(INV >> (4 * (hl & 15u))) & 15u];
-      const int beta = ffs32(~cE & (uint32_t)tb.triEdges[j]);
-      const int w = beta == tb.triA[j] ? 0 : 1;
-      eCode |= (uint64_t)(tb.cofIdx[j][w] + 1) * tb.nib[beta];
-      classify_tri(j);
-      // the other triangles of PQone on beta have no unclassified edge
-      // left: they go to PQzero now rather than when popped.  They are
-      // not the minimum of PQone before then, and PQzero is not popped
-      // while PQone holds anything, so the sequence of pairs is the same.
-      uint64_t z = classify_edge(beta) & TL & ~tb.bit[j];
-      zT |= z;
-      for (; z; z &= z - 1) {
-        const uint32_t p = tri_pos(ffs64(z));
-        pP0 &= ~tb.posLo[p];
-        pP1 &= ~tb.posHi[p];
-      }
-      zE &= ~(1u << beta);
-      pQ |= tb.triCof[j] & QL & Q2 & ~Q3 & ~cQ;
-      push_tris(tb.edgeCof[beta] & TL & C1 & ~C2);
+    // Prim: the frontier edge of smallest key classifies its unclassified end
+    for (;;) {
+      const uint32_t F0 = E0 & I0 & ~N0, F1 = E1 & I1 & ~N1, F2 = E2 & I2 & ~N2;
+      if (!(F0 | F1 | F2)) break;
+      const uint32_t p = F0 ? (uint32_t)ffs32(F0) : (F1 ? 32u + ffs32(F1) : 64u + ffs32(F2));
+      const uint32_t hl = tb.hlOfPos[p], h = hl >> 4, l = hl & 15u;
+      const uint32_t u = ((C >> h) & 1u) ? l : h;  // the new vertex
+      const int su = slot(u), sw = slot(u ^ h ^ l);
+      const int j = tb.triOfSlots[su][sw];
+      eCode |= (uint64_t)(tb.cofOfSlots[su][sw] + 1u) * tb.nib[su];
+      classify_vertex(u);
+      mark_pos(p);
+      classify_edge(j);
     }
-    while (pQ) {
+    // the component's link triangles and cycle edges
+    uint32_t pQ = QL & Q2 & ~Q3 & ~cQ;
+    for (;;) {
+      while (pQ) {
+        uint32_t bestQ = 0xFFFFu;
+        int q = 0;
+        for (uint32_t m = pQ; m; m &= m - 1) {
+          const int qq = ffs32(m);
+          const uint32_t kq = tet_key(qq);
+          if (kq < bestQ) { bestQ = kq; q = qq; }
+        }
+        pQ &= ~(1u << q);
+        if ((Q3 >> q) & 1) continue;  // no unclassified edge left: PQzero
+        const int beta = ffs64(~cT & tb.tetFmask[q]);
+        const int w = beta == tb.tetF[q][0] ? 0 : (beta == tb.tetF[q][1] ? 1 : 2);
+        set_tet_code(q, tb.tetCode[q][w]);
+        cQ |= 1u << q;
+        classify_edge(beta);
+        mark_pos(pos_of(rank(tb.triA[beta]), rank(tb.triB[beta])));
+        pQ |= tb.triCof[beta] & QL & Q2 & ~Q3 & ~cQ;
+      }
+      // PQzero: the smallest unclassified cycle edge or fully bounded tet
+      const uint32_t Z0 = E0 & N0 & ~K0, Z1 = E1 & N1 & ~K1, Z2 = E2 & N2 & ~K2;
+      const uint32_t zQ = QL & Q3 & ~cQ;
+      if (!(Z0 | Z1 | Z2 | zQ)) break;
+      uint32_t bestE = 0xFFFFu, pe = 0;
+      if (Z0 | Z1 | Z2) {
+        pe = Z0 ? (uint32_t)ffs32(Z0) : (Z1 ? 32u + ffs32(Z1) : 64u + ffs32(Z2));
+        const uint32_t hl = tb.hlOfPos[pe];
+        bestE = (((hl >> 4) + 1) << 8) | (((hl & 15u) + 1) << 4);
+      }
       uint32_t bestQ = 0xFFFFu;
       int q = 0;
-      for (uint32_t m = pQ; m; m &= m - 1) {
+      for (uint32_t m = zQ; m; m &= m - 1) {
         const int qq = ffs32(m);
-        const uint32_t k = tet_key(qq);
-        if (k < bestQ) { bestQ = k; q = qq; }
+        const uint32_t kq = tet_key(qq);
+        if (kq < bestQ) { bestQ = kq; q = qq; }
       }
-      pQ &= ~(1u << q);
-      if ((Q3 >> q) & 1) { zQ |= 1u << q; continue; }  // nuf == 0
-      const int beta = ffs64(~cT & tb.tetFmask[q]);
-      const int w = beta == tb.tetF[q][0] ? 0 : (beta == tb.tetF[q][1] ? 1 : 2);
-      set_tet_code(q, tb.tetCode[q][w]);
-      classify_tri(beta);
-      cQ |= 1u << q;
-      zT &= ~tb.bit[beta];
-      pQ |= tb.triCof[beta] & QL & Q2 & ~Q3 & ~cQ;
+      if (bestE < bestQ) {  // a critical link edge: a critical triangle of L
+        const uint32_t hl = tb.hlOfPos[pe];
+        const int j = tb.triOfSlots[slot(hl >> 4)][slot(hl & 15u)];
+        critT |= 1ull << j;
+        classify_edge(j);
+        mark_pos(pe);
+        pQ = tb.triCof[j] & QL & Q2 & ~Q3 & ~cQ;
+      } else {  // a critical link triangle: a critical tet of L
+        cQ |= 1u << q;
+        set_tet_code(q, 7u);
+      }
     }
-    if (!(zE | zT | zQ)) break;
-    // pop-min of PQzero: the next critical simplex
-    uint32_t best = 0xFFFFu;
-    int bi = 0, bd = 0;
-    for (uint32_t m = zE; m; m &= m - 1) {
-      int s = ffs32(m);
-      uint32_t k = (rank(s) + 1) << 8;
-      if (k < best) { best = k; bi = s; bd = 1; }
-    }
-    for (uint64_t m = zT; m; m &= m - 1) {
-      int j = ffs64(m);
-      uint32_t k = pos_key(tri_pos(j));
-      if (k < best) { best = k; bi = j; bd = 2; }
-    }
-    for (uint32_t m = zQ; m; m &= m - 1) {
-      int q = ffs32(m);
-      uint32_t k = tet_key(q);
-      if (k < best) { best = k; bi = q; bd = 3; }
-    }
-    if (bd == 1) {
-      zE &= ~(1u << bi);
-      eCode |= 7ull << (4 * bi);
-      classify_edge(bi);
-      push_tris(tb.edgeCof[bi] & TL & C1 & ~C2);
-    } else if (bd == 2) {
-      zT &= ~(1ull << bi);
-      critT |= 1ull << bi;
-      classify_tri(bi);
-      pQ |= tb.triCof[bi] & QL & Q2 & ~Q3 & ~cQ;
-    } else {
-      zQ &= ~(1u << bi);
-      cQ |= 1u << bi;
-      set_tet_code(bi, 7u);
-    }
+    // the next component: its lowest vertex is a critical edge of L
+    const uint32_t rem = ((1u << k) - 1u) & ~C;
+    if (!rem) break;
+    const uint32_t r = (uint32_t)ffs32(rem);
+    eCode |= 7ull << (4 * slot(r));
+    classify_vertex(r);
   }
 
-  // encode: every simplex of L is written once, at its anchor (codes of
-  // slots and tets outside L are 0)
   static_for<0, 14>([&](auto S) {
     constexpr int s = decltype(S)::value;
     constexpr int ec = kStar.eCorner[s], et = kStar.eType[s];
@@ -331,20 +314,21 @@ DMS_HD int process_lower_star(uint32_t lm, const uint32_t (&o)[14], const Tables
       if ((critT >> j) & 1) acc[tc] |= 1ull << (21 + tt);
     });
   }
-  static_for<0, 24>([&](auto Q) {
-    constexpr int q = decltype(Q)::value;
-    constexpr int qc = kStar.qCorner[q], qt = kStar.qType[q];
-    uint64_t code;
-    if constexpr (q < 16) code = (qCode0 >> (4 * q)) & 7ull;
-    else code = (uint64_t)((qCode1 >> (4 * (q - 16))) & 7u);
-    acc[qc] |= code << (33 + 3 * qt);
-  });
+  if (QL) {
+    static_for<0, 24>([&](auto Q) {
+      constexpr int q = decltype(Q)::value;
+      constexpr int qc = kStar.qCorner[q], qt = kStar.qType[q];
+      uint64_t code;
+      if constexpr (q < 16) code = (qCode0 >> (4 * q)) & 7ull;
+      else code = (uint64_t)((qCode1 >> (4 * (q - 16))) & 7u);
+      acc[qc] |= code << (33 + 3 * qt);
+    });
+  }
   return delta;
 }
 
 constexpr Tables make_tables() {
   Tables t{};
-  for (int i = 0; i < 14; ++i) t.edgeCof[i] = kStar.edgeCof[i];
   for (int i = 0; i < 24; ++i) {
     t.tetFmask[i] = kStar.tetFmask[i];
     for (int w = 0; w < 3; ++w) {
@@ -357,25 +341,28 @@ constexpr Tables make_tables() {
   }
   for (int i = 0; i < 36; ++i) {
     t.triCof[i] = kStar.triCof[i];
-    t.triEdges[i] = (uint16_t)kStar.triEdges[i];
     t.triA[i] = (uint8_t)kStar.triA[i];
     t.triB[i] = (uint8_t)kStar.triB[i];
-    t.cofIdx[i][0] = (uint8_t)kStar.cofIdx[i][0];
-    t.cofIdx[i][1] = (uint8_t)kStar.cofIdx[i][1];
   }
   for (int a = 0; a < 14; ++a)
-    for (int b = 0; b < 14; ++b) t.triOfSlots[a][b] = 255;
+    for (int b = 0; b < 14; ++b) t.triOfSlots[a][b] = t.cofOfSlots[a][b] = 255;
   for (int i = 0; i < 36; ++i) {
     t.triOfSlots[kStar.triA[i]][kStar.triB[i]] = (uint8_t)i;
     t.triOfSlots[kStar.triB[i]][kStar.triA[i]] = (uint8_t)i;
+    t.cofOfSlots[kStar.triA[i]][kStar.triB[i]] = (uint8_t)kStar.cofIdx[i][0];
+    t.cofOfSlots[kStar.triB[i]][kStar.triA[i]] = (uint8_t)kStar.cofIdx[i][1];
   }
   for (int h = 1; h < 14; ++h)
     for (int l = 0; l < h; ++l) t.hlOfPos[h * (h - 1) / 2 + l] = (uint8_t)((h << 4) | l);
   for (int i = 0; i < 64; ++i) t.bit[i] = 1ull << i;
   for (int i = 0; i < 16; ++i) t.nib[i] = 1ull << (4 * i);
-  for (int p = 0; p < 91; ++p) {
-    t.posLo[p] = p < 64 ? 1ull << p : 0;
-    t.posHi[p] = p < 64 ? 0 : 1ull << (p - 64);
+  for (int r = 0; r < 14; ++r) {
+    for (int w = 0; w < 4; ++w) t.star[r][w] = 0;
+    for (int x = 0; x < 14; ++x) {
+      if (x == r) continue;
+      const int h = r > x ? r : x, l = r > x ? x : r, pos = h * (h - 1) / 2 + l;
+      t.star[r][pos >> 5] |= 1u << (pos & 31);
+    }
   }
   for (int m = 0; m < 128; ++m) {
     t.notTlo[m] = t.notThi[m] = 0;

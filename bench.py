@@ -411,6 +411,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-field batch leg")
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiable leg")
     ap.add_argument("--no-2d", action="store_true", help="skip the 2D leg")
+    ap.add_argument("--no-pairing-cmp", action="store_true",
+                    help="skip the D0/D2 pairing comparison (rounds vs self-correcting)")
     ap.add_argument("--with-d1", action="store_true",
                     help="add the D1 leg (saddle-saddle pairs, 256^3 quantised noise)")
     ap.add_argument("--leg", choices=["batched", "diff", "2d", "d1"], default=None,
@@ -528,7 +530,7 @@ def main():
     # (spanning forest, then exact rounds) and the paper's self-correcting
     # pairing (Alg. 4) as a fixpoint, on the same gradient
     pairing_cmp = None
-    if world == 1:
+    if world == 1 and not args.no_pairing_cmp:
         o_ = dms.order(f)
         g_ = dms.gradient(o_)
         c_ = dms.critical(g_)

@@ -4,15 +4,12 @@
 // (the stratification of Sec. 2.5) by homologous propagation.
 //
 // Every such triangle sigma is a column whose boundary -- initially the three
-// edges of sigma -- is kept, Z2, as a sorted run (decreasing lexicographic
-// key of Sec. 2.1, no edge twice; the highest edge at its front) plus a
-// small binary max-heap of recent insertions in which an edge may sit
-// several times (copies cancel in pairs when they reach the top).  A full
-// heap is flushed into the run by one linear merge, and adding another
-// column's boundary is one linear merge of two runs, so a large boundary
-// costs sequential passes rather than one heap operation per edge
-// ("Z2" and "cancel": an edge present an even number of times is absent).
-// All columns work at once, in rounds of two kernels:
+// edges of sigma -- lives in a binary max-heap of edges keyed by their
+// lexicographic key (orders of the two vertices, higher first; Sec. 2.1) in
+// a pool of device memory.  Z2 arithmetic is lazy: an edge added twice sits
+// twice in the heap and the copies cancel when they reach the top; a heap
+// about to outgrow its segment is first compacted (sorted in place, pairs
+// cancelled).  All columns work at once, in rounds of two kernels:
 //   advance  a column expands its boundary at the highest edge tau: while
 //            tau is not critical it is paired with a triangle by the
 //            gradient, whose boundary is added (its other two edges are
@@ -131,16 +128,12 @@ static_assert(sizeof(HEnt) == 16, "heap entry");
 // one column (a D2-unpaired critical triangle)
 struct Col {
   unsigned long long key;  // the triangle's lexicographic key in 40 bits
-  unsigned long long run;  // pool offset of the sorted run: entries [rbeg, rlen)
-  unsigned long long alt;  // pool offset of the spare run buffer (same capacity)
-  unsigned long long heap; // pool offset of the small heap: hsize of hcap used
-  uint32_t rbeg, rlen, rcap;
-  uint32_t hsize, hcap;
+  unsigned long long off;  // its heap: pool[off, off + cap), size entries used
+  uint32_t size, cap;
   uint32_t pivot;  // index in crit1 of the current pivot, kNone if none
   uint32_t state;  // 0 not a column (D2-paired), 1 active, 2 failed
-  uint32_t pad;
 };
-static_assert(sizeof(Col) == 64, "column");
+static_assert(sizeof(Col) == 32, "column");
 
 struct D1Ws {
   uint8_t* d0mark;    // [n1]: the critical edge is a D0 death
@@ -157,9 +150,6 @@ struct D1Ws {
 };
 
 constexpr int WNT = 256, WITEMS = 16, WTILE = WNT * WITEMS;
-constexpr uint32_t kRun0 = 4;   // first run buffers (two) of every column
-constexpr uint32_t kHeap0 = 8;  // and its first heap
-constexpr uint32_t kStride0 = 2 * kRun0 + kHeap0;
 
 D1Ws carve(void* base, int64_t n1, int64_t n2, int64_t pool_entries) {
   WsCarver c(base);
@@ -220,7 +210,7 @@ __device__ __forceinline__ void ent_edge(const Grid& g, const HEnt& e, int64_t& 
   a = e.s < 7 ? (int64_t)e.v : (int64_t)e.v - cdelta(g, corner_of_type(k));
 }
 
-// ---- boundaries: a sorted run plus a small heap, in the pool -----------------
+// ---- heap in the pool -------------------------------------------------------
 __device__ __forceinline__ void heap_push(HEnt* h, uint32_t& size, const HEnt& e) {
   uint32_t i = size++;
   while (i > 0) {
@@ -247,122 +237,44 @@ __device__ __forceinline__ HEnt heap_pop(HEnt* h, uint32_t& size) {
   return top;
 }
 
-// pool space (bump allocation; false when the pool is exhausted)
-__device__ __forceinline__ bool pool_take(D1Ws& w, uint64_t n, unsigned long long& off) {
-  off = atomicAdd(w.ctr + 0, (unsigned long long)n);
-  return off + n <= (unsigned long long)w.pool_cap;
-}
-
-// run buffers of at least `need` entries (a fresh pair when the current one
-// is too small; the run being read stays where it is)
-__device__ __forceinline__ bool ensure_alt(D1Ws& w, Col& c, uint64_t need) {
-  if (need <= c.rcap) return true;
-  const uint64_t cap = std::max<uint64_t>(2ull * c.rcap, need);
-  if (cap > 0xFFFFFFFFull) return false;
-  unsigned long long off;
-  if (!pool_take(w, 2 * cap, off)) return false;
-  c.alt = off;  // the new pair: alt now, the other half is the next spare
-  c.rcap = (uint32_t)cap;
-  c.pad = 1;    // the run still lives in the old pair: after the merge the
-                // spare is alt + cap (see finish_merge)
-  return true;
-}
-
-// after writing the merged run to c.alt: it becomes the run
-__device__ __forceinline__ void finish_merge(Col& c, uint32_t n) {
-  const unsigned long long old = c.run;
-  c.run = c.alt;
-  c.alt = c.pad ? c.alt + c.rcap : old;
-  c.pad = 0;
-  c.rbeg = 0;
-  c.rlen = n;
-}
-
-// Z2 merge of two decreasing sequences read by `a(i)` / `b(j)` into out:
-// an edge present an odd number of times in total is written once
-template <class A, class B>
-__device__ __forceinline__ uint32_t merge_desc(A a, uint32_t na, B b, uint32_t nb, HEnt* out) {
-  uint32_t i = 0, j = 0, n = 0;
-  while (i < na || j < nb) {
-    unsigned long long key;
-    HEnt e;
-    if (j >= nb || (i < na && a(i).key >= b(j).key)) {
-      e = a(i);
-    } else {
-      e = b(j);
-    }
-    key = e.key;
-    uint32_t cnt = 0;
-    while (i < na && a(i).key == key) { ++i; ++cnt; }
-    while (j < nb && b(j).key == key) { ++j; ++cnt; }
-    if (cnt & 1) out[n++] = e;
-  }
-  return n;
-}
-
-// the heap into the run (heapsort of the heap, then one merge)
-__device__ __forceinline__ bool flush(D1Ws& w, Col& c) {
-  if (c.hsize == 0) return true;
-  HEnt* h = w.pool + c.heap;
-  uint32_t n = c.hsize;
-  while (n > 1) {  // heapsort: increasing in place
-    const HEnt top = heap_pop(h, n);
+// sorts a heap in place (heapsort, ascending), cancels equal pairs (Z2) and
+// leaves the survivors in decreasing order, which is a max-heap again
+__device__ __forceinline__ void heap_compact(HEnt* h, uint32_t& size) {
+  uint32_t n = size;
+  while (n > 1) {
+    const HEnt top = heap_pop(h, n);  // n decreases by one
     h[n] = top;
   }
-  const uint32_t hs = c.hsize, rn = c.rlen - c.rbeg;
-  if (!ensure_alt(w, c, (uint64_t)rn + hs)) return false;
-  const HEnt* run = w.pool + c.run + c.rbeg;
-  const uint32_t m = merge_desc([&](uint32_t i) { return run[i]; }, rn,
-                                [&](uint32_t j) { return h[hs - 1 - j]; }, hs, w.pool + c.alt);
-  finish_merge(c, m);
-  c.hsize = 0;
-  // a large run gets a larger heap, so flushes stay rare against its size
-  if (m > 8u * c.hcap && c.hcap < (1u << 20)) {
-    unsigned long long off;
-    if (!pool_take(w, 2ull * c.hcap, off)) return false;
-    c.heap = off;
-    c.hcap *= 2;
+  uint32_t m = 0;
+  for (uint32_t i = 0; i < size;) {
+    uint32_t j = i + 1;
+    while (j < size && h[j].key == h[i].key) ++j;
+    if ((j - i) & 1) h[m++] = h[i];
+    i = j;
   }
-  return true;
+  for (uint32_t i = 0; i < m / 2; ++i) {
+    const HEnt t = h[i];
+    h[i] = h[m - 1 - i];
+    h[m - 1 - i] = t;
+  }
+  size = m;
 }
 
-__device__ __forceinline__ bool push(D1Ws& w, Col& c, const HEnt& e) {
-  if (c.hsize == c.hcap && !flush(w, c)) return false;
-  heap_push(w.pool + c.heap, c.hsize, e);
-  return true;
-}
-
-// pops the highest edge with all its copies; false if the boundary is empty
-__device__ __forceinline__ bool pop_top(D1Ws& w, Col& c, HEnt& e, bool& odd) {
-  const HEnt* run = w.pool + c.run;
-  HEnt* h = w.pool + c.heap;
-  const unsigned long long kr = c.rbeg < c.rlen ? run[c.rbeg].key : 0ull;
-  const unsigned long long kh = c.hsize ? h[0].key : 0ull;
-  if (!kr && !kh) return false;  // keys are > 0: an edge's top has order >= 1
-  const unsigned long long key = kr > kh ? kr : kh;
-  uint32_t cnt = 0;
-  if (kr == key) {
-    e = run[c.rbeg++];
-    ++cnt;
-  }
-  while (c.hsize && h[0].key == key) {
-    e = heap_pop(h, c.hsize);
-    ++cnt;
-  }
-  odd = cnt & 1;
-  return true;
-}
-
-// adds column o's boundary (a flushed, settled column: its run only)
-__device__ __forceinline__ bool add_column(D1Ws& w, Col& c, const Col& o) {
-  if (!flush(w, c)) return false;
-  const uint32_t rn = c.rlen - c.rbeg, on = o.rlen - o.rbeg;
-  if (!ensure_alt(w, c, (uint64_t)rn + on)) return false;
-  const HEnt* run = w.pool + c.run + c.rbeg;
-  const HEnt* other = w.pool + o.run + o.rbeg;
-  const uint32_t m = merge_desc([&](uint32_t i) { return run[i]; }, rn,
-                                [&](uint32_t j) { return other[j]; }, on, w.pool + c.alt);
-  finish_merge(c, m);
+// room for `more` entries: compact the heap, and if that is not enough move
+// it to a larger segment of the pool
+__device__ __forceinline__ bool heap_reserve(D1Ws& w, Col& c, uint32_t more) {
+  if ((uint64_t)c.size + more <= c.cap) return true;
+  heap_compact(w.pool + c.off, c.size);
+  if ((uint64_t)c.size + more <= c.cap && 4ull * c.size <= 3ull * c.cap) return true;
+  uint64_t ncap = std::max<uint64_t>(2ull * c.cap, (uint64_t)c.size + more);
+  if (ncap > 0xFFFFFFFFull) return false;
+  const unsigned long long off = atomicAdd(w.ctr + 0, (unsigned long long)ncap);
+  if (off + ncap > (unsigned long long)w.pool_cap) return false;
+  HEnt* src = w.pool + c.off;
+  HEnt* dst = w.pool + off;
+  for (uint32_t i = 0; i < c.size; ++i) dst[i] = src[i];
+  c.off = off;
+  c.cap = (uint32_t)ncap;
   return true;
 }
 
@@ -409,9 +321,10 @@ __device__ __forceinline__ uint32_t rank_below(const Grid& g, const uint32_t* __
   return r;
 }
 
-// the columns: key, and a run holding the three edges of the triangle
+// the columns: key, and a heap holding the three edges of the triangle
 __global__ void init_cols(Grid g, const uint32_t* __restrict__ order,
-                          const int64_t* __restrict__ crit2, int64_t n2, D1Ws w) {
+                          const int64_t* __restrict__ crit2, int64_t n2, D1Ws w, uint32_t cap0,
+                          int32_t* dstatus) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n2;
        j += (int64_t)gridDim.x * blockDim.x) {
     Col c = w.col[j];
@@ -430,31 +343,18 @@ __global__ void init_cols(Grid g, const uint32_t* __restrict__ order,
     const uint32_t hi = max(oa, ob), lo = min(oa, ob);
     c.key = ((unsigned long long)o[it] << 8) | (rank_below(g, order, v[it], hi) << 4) |
             rank_below(g, order, v[it], lo);
-    const unsigned long long base = (unsigned long long)j * kStride0;
-    c.run = base;
-    c.alt = base + kRun0;
-    c.heap = base + 2 * kRun0;
-    c.rcap = kRun0;
-    c.hcap = kHeap0;
-    c.hsize = 0;
-    c.pad = 0;
+    c.off = (unsigned long long)j * cap0;
+    c.cap = cap0;
+    c.size = 0;
     c.pivot = kNone;
     c.state = 1;
-    HEnt e[3] = {make_ent(order, g, b, p), make_ent(order, g, b, q),
-                 make_ent(order, g, v[1], q ^ p)};
-    for (int i = 0; i < 3; ++i)  // decreasing keys (three distinct edges)
-      for (int k2 = i + 1; k2 < 3; ++k2)
-        if (e[k2].key > e[i].key) {
-          const HEnt tmp = e[i];
-          e[i] = e[k2];
-          e[k2] = tmp;
-        }
-    HEnt* run = w.pool + c.run;
-    for (int i = 0; i < 3; ++i) run[i] = e[i];
-    c.rbeg = 0;
-    c.rlen = 3;
+    HEnt* h = w.pool + c.off;
+    heap_push(h, c.size, make_ent(order, g, b, p));
+    heap_push(h, c.size, make_ent(order, g, b, q));
+    heap_push(h, c.size, make_ent(order, g, v[1], q ^ p));
     w.col[j] = c;
   }
+  (void)dstatus;
 }
 
 // expands a column's boundary until its highest edge is a critical D1
@@ -469,14 +369,19 @@ __device__ __forceinline__ bool expand_col(const Grid& g, const uint32_t* __rest
       fail(w, c, dstatus, DMS_ERR_TIMEOUT);
       return false;
     }
-    // the highest edge, with its copies (Z2: an even count cancels)
-    HEnt e;
-    bool odd;
-    if (!pop_top(w, c, e, odd)) {  // a D2-unpaired triangle kills a cycle: not reached
+    HEnt* h = w.pool + c.off;
+    if (c.size == 0) {  // a D2-unpaired triangle kills a cycle: not reached
       fail(w, c, dstatus, DMS_ERR_ARG);
       return false;
     }
-    if (!odd) continue;
+    // the highest edge, with its copies (Z2: an even count cancels)
+    const HEnt e = heap_pop(h, c.size);
+    uint32_t copies = 1;
+    while (c.size && h[0].key == e.key) {
+      heap_pop(h, c.size);
+      ++copies;
+    }
+    if (!(copies & 1)) continue;
     int64_t a;
     int k;
     ent_edge(g, e, a, k);
@@ -487,10 +392,7 @@ __device__ __forceinline__ bool expand_col(const Grid& g, const uint32_t* __rest
         fail(w, c, dstatus, DMS_ERR_ARG);
         return false;
       }
-      if (!push(w, c, e)) {
-        fail(w, c, dstatus, DMS_ERR_CAPACITY);
-        return false;
-      }
+      heap_push(h, c.size, e);
       c.pivot = (uint32_t)idx;
       return true;
     }
@@ -505,18 +407,18 @@ __device__ __forceinline__ bool expand_col(const Grid& g, const uint32_t* __rest
     const int p = tri_p(t), q = tri_q(t);
     const HEnt f[3] = {make_ent(order, g, tb, p), make_ent(order, g, tb, q),
                        make_ent(order, g, tb + cdelta(g, p), q ^ p)};
+    if (!heap_reserve(w, c, 2)) {
+      fail(w, c, dstatus, DMS_ERR_CAPACITY);
+      return false;
+    }
+    h = w.pool + c.off;
     for (int i = 0; i < 3; ++i)
-      if (f[i].key != e.key && !push(w, c, f[i])) {
-        fail(w, c, dstatus, DMS_ERR_CAPACITY);
-        return false;
-      }
+      if (f[i].key != e.key) heap_push(h, c.size, f[i]);
   }
 }
 
-// one round for every column that has not settled: expand, add the
-// boundaries of earlier columns settled on its pivot, claim the rest.  A
-// column that stops on a pivot it holds or claims flushes its heap first,
-// so that a column reading it next round reads one run.
+// one round for every column that has not settled: expand, merge the
+// boundaries of earlier columns settled on its pivot, claim the rest
 __global__ void __launch_bounds__(256) advance(Grid g, const uint32_t* __restrict__ order,
                                                const uint64_t* __restrict__ rec,
                                                const int64_t* __restrict__ crit1, int64_t n1,
@@ -531,24 +433,24 @@ __global__ void __launch_bounds__(256) advance(Grid g, const uint32_t* __restric
       if (c.pivot == kNone && !expand_col(g, order, rec, crit1, n1, w, c, steps, limit, dstatus))
         break;
       const unsigned long long o = w.owner_key[c.pivot];
-      if (o >= c.key) {  // held by this column, unclaimed, or a later one holds it
-        if (!flush(w, c)) {
-          fail(w, c, dstatus, DMS_ERR_CAPACITY);
-          break;
-        }
-        if (o > c.key) atomicMin(w.owner_key + c.pivot, c.key);
+      if (o == c.key) break;  // claimed by this column: settles at publish
+      if (o > c.key) {        // unclaimed, or a later column holds it: claim
+        atomicMin(w.owner_key + c.pivot, c.key);
         break;
       }
       // an earlier column holds the pivot: add its boundary if it settled
-      // on it in the last publish (its run is then left alone this round)
+      // on it in the last publish (its heap is then left alone this round)
       const uint32_t oc = w.owner_col[c.pivot];
       if (oc >= (uint64_t)n2 || !w.settled[oc]) break;
       const Col oo = w.col[oc];
-      if (oo.key != o || oo.pivot != c.pivot || oo.hsize != 0) break;
-      if (!add_column(w, c, oo)) {
+      if (oo.key != o || oo.pivot != c.pivot) break;
+      if (!heap_reserve(w, c, oo.size)) {
         fail(w, c, dstatus, DMS_ERR_CAPACITY);
         break;
       }
+      HEnt* h = w.pool + c.off;
+      const HEnt* src = w.pool + oo.off;
+      for (uint32_t i = 0; i < oo.size; ++i) heap_push(h, c.size, src[i]);
       c.pivot = kNone;
     }
     w.col[j] = c;
@@ -652,7 +554,7 @@ __global__ void init_state(Col* col, int64_t n2) {
     col[i].state = 1;
 }
 
-constexpr uint32_t kCap0 = kStride0;
+constexpr uint32_t kCap0 = 16;        // first heap segment of every column
 constexpr int kMaxRounds = 4096;      // reduction rounds before DMS_ERR_TIMEOUT
 constexpr int64_t kExpandLimit = 1ll << 26;  // heap pops of one column in one round
 
@@ -695,7 +597,7 @@ int launch_d1(const float* f, const uint32_t* order, const uint64_t* rec, const 
   }
   const unsigned long long cursor0 = (unsigned long long)n2 * kCap0;
   DMS_CUDA_OK(cudaMemcpyAsync(w.ctr + 0, &cursor0, sizeof(cursor0), cudaMemcpyHostToDevice, s));
-  init_cols<<<nb(n2), TB, 0, s>>>(g, order, crit2, n2, w); count_launch();
+  init_cols<<<nb(n2), TB, 0, s>>>(g, order, crit2, n2, w, kCap0, dstatus); count_launch();
   DMS_CUDA_OK(cudaMemsetAsync(w.settled, 0, std::max<int64_t>(n2, 1), s));
   for (int round = 1;; ++round) {
     if (round > kMaxRounds) return DMS_ERR_TIMEOUT;

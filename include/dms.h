@@ -305,10 +305,12 @@ int dms_diagram_d1(const float* f, const uint32_t* order, const uint64_t* rec, d
  *                larger capacities).
  *   ws           at least dms_batch_workspace_size(...) bytes.
  * The spanning forest takes a fixed 40 Boruvka rounds (enough: the active
- * components at least halve per round); the pairing runs at most
- * dms_batch_max_rounds() rounds and then finishes at most 4096 saddles in
- * order; beyond that (1 << DMS_ERR_TIMEOUT) is set and the per-field entry
- * points should be used.
+ * components at least halve per round); the pairing runs
+ * dms_batch_max_rounds() exact rounds and finishes the saddles still live
+ * in increasing weight (Alg. 1's own order): up to 4096 of them in one CTA,
+ * more after a device-wide sort by one thread, which is slow when very many
+ * are left (a chain of components that the exact rounds merge one per
+ * round) but exact.
  */
 int32_t dms_batch_tile_variants(void);
 int32_t dms_batch_max_rounds(void);

@@ -1425,11 +1425,8 @@ __global__ void __launch_bounds__(1024) b_finish(const uint32_t* __restrict__ li
   __shared__ unsigned long long key[kFinishMax];
   __shared__ uint32_t idx[kFinishMax];
   const unsigned int n = *live_n;
-  if (n == 0) return;
-  if (n > (unsigned)kFinishMax) {
-    if (threadIdx.x == 0) set_status(dstatus, DMS_ERR_TIMEOUT);
-    return;
-  }
+  if (n == 0 || n > (unsigned)kFinishMax) return;  // more: the sorted finish below
+  (void)dstatus;
   for (int i = threadIdx.x; i < kFinishMax; i += blockDim.x) {
     key[i] = i < (int)n ? T.s[live[i]].w : ~0ull;
     idx[i] = i < (int)n ? live[i] : kNone;
@@ -1463,6 +1460,15 @@ __global__ void __launch_bounds__(1024) b_finish(const uint32_t* __restrict__ li
     const uint32_t young = nd.age[a] > nd.age[b] ? a : b;
     nd.parent[young] = young == a ? b : a;
     T.s[i].res = young;
+  }
+}
+
+// the count of live saddles left to the device-wide sorted finish (those
+// the one-CTA finish does not take), for the kernels that read it
+__global__ void b_big_count(const unsigned int* __restrict__ live_n, unsigned int* big_n) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const unsigned int n = *live_n;
+    *big_n = n > (unsigned)kFinishMax ? n : 0u;
   }
 }
 
@@ -1647,6 +1653,14 @@ int launch_diagram_batch(const float* f, const uint32_t* order, const uint8_t* d
       std::swap(cur_n, nxt_n);
     }
     b_finish<<<1, 1024, 0, s>>>(cur, cur_n, T, w.nd, dstatus); count_launch();
+    // more than the one-CTA finish holds: sort them by weight on the device
+    // and finish them in that order (one thread; nothing runs when the
+    // count is small)
+    unsigned int* big_n = w.ctr + 4;
+    b_big_count<<<1, 32, 0, s>>>(cur_n, big_n); count_launch();
+    gather_live<<<G, TB, 0, s>>>(cur, big_n, T, w.rb.ka, w.rb.va); count_launch();
+    const bool in_a = radix64::sort(w.rb, nsad, 44, s, big_n);
+    sequential_finish<<<1, 32, 0, s>>>(in_a ? w.rb.va : w.rb.vb, big_n, T, w.nd); count_launch();
   };
   auto write = [&](int dim, Tri T, const int64_t* critA, const int64_t* critB, const int64_t* n_dev,
                    dms_pair* out, int64_t* offs, int64_t* total, unsigned long long* fc) {

@@ -17,8 +17,12 @@ constexpr int ITEMS = 16;
 constexpr int TILE = NT * ITEMS;  // 4096
 constexpr int WARPS = NT / 32;
 
+// n_dev, if given, is a device count that caps n (launches sized for a
+// capacity, the count known only on the device)
 __global__ void __launch_bounds__(NT) upsweep(const unsigned long long* __restrict__ keys, int64_t n,
-                                              int shift, int64_t ntiles, long long* __restrict__ th) {
+                                              int shift, int64_t ntiles, long long* __restrict__ th,
+                                              const unsigned int* n_dev = nullptr) {
+  if (n_dev && (int64_t)*n_dev < n) n = *n_dev;
   __shared__ unsigned int h[WARPS][256];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < WARPS * 256; i += NT) (&h[0][0])[i] = 0;
@@ -52,7 +56,9 @@ __global__ void __launch_bounds__(NT) downsweep(const unsigned long long* __rest
                                                 const uint32_t* __restrict__ vin,
                                                 unsigned long long* __restrict__ kout,
                                                 uint32_t* __restrict__ vout, int64_t n, int shift,
-                                                int64_t ntiles, const long long* __restrict__ th) {
+                                                int64_t ntiles, const long long* __restrict__ th,
+                                                const unsigned int* n_dev = nullptr) {
+  if (n_dev && (int64_t)*n_dev < n) n = *n_dev;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   DownSmem& sm = *reinterpret_cast<DownSmem*>(smem_raw);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -147,8 +153,10 @@ inline Buffers carve(WsCarver& c, int64_t n) {
 }
 
 // Sorts b.ka/b.va (n entries) on key bits [0, bits); returns true if the
-// result ended in ka/va, false if in kb/vb.
-inline bool sort(Buffers& b, int64_t n, int bits, cudaStream_t s) {
+// result ended in ka/va, false if in kb/vb.  With n_dev the entry count is
+// *n_dev (read on the device, at most n): nothing synchronises the host.
+inline bool sort(Buffers& b, int64_t n, int bits, cudaStream_t s,
+                 const unsigned int* n_dev = nullptr) {
   static bool configured = false;
   if (!configured) {
     cudaFuncSetAttribute(downsweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -164,9 +172,10 @@ inline bool sort(Buffers& b, int64_t n, int bits, cudaStream_t s) {
     uint32_t* vi = in_a ? b.va : b.vb;
     unsigned long long* ko = in_a ? b.kb : b.ka;
     uint32_t* vo = in_a ? b.vb : b.va;
-    upsweep<<<(unsigned)ntiles, NT, 0, s>>>(ki, n, shift, ntiles, b.th); count_launch();
+    upsweep<<<(unsigned)ntiles, NT, 0, s>>>(ki, n, shift, ntiles, b.th, n_dev); count_launch();
     scan64::run(b.th, m, b.sums, s);
-    downsweep<<<(unsigned)ntiles, NT, sizeof(DownSmem), s>>>(ki, vi, ko, vo, n, shift, ntiles, b.th); count_launch();
+    downsweep<<<(unsigned)ntiles, NT, sizeof(DownSmem), s>>>(ki, vi, ko, vo, n, shift, ntiles, b.th,
+                                                            n_dev); count_launch();
     in_a = !in_a;
   }
   return in_a;

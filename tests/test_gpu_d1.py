@@ -72,3 +72,28 @@ def test_d1_pool_too_small_then_grown():
     d1 = dms.diagram_d1(f, r.order, r.grad, r.crit, r.diagrams, pool_entries=16 * n2 + 64)
     torch.cuda.synchronize()
     _same_pairs(d1.cpu().numpy().view(dms.PAIR_DTYPE).reshape(-1), ref)
+
+
+def test_d1_properties_at_160_cubed_quantised_noise():
+    """Beyond the oracle's reach, what holds at any size: every critical edge
+    is in exactly one of D0 and D1, every critical triangle in exactly one
+    of D1 and D2, the births are distinct, each death follows its birth in
+    the filtration, and the values are the field's at the carriers."""
+    f = fields.config2(0, "cuda", n=160)
+    r = dms.diagram(f)
+    d1 = dms.diagram_d1(f, r.order, r.grad, r.crit, r.diagrams)
+    torch.cuda.synchronize()
+    p = d1.cpu().numpy().view(dms.PAIR_DTYPE).reshape(-1)
+    c1, c2 = r.crit[1].cpu().numpy(), r.crit[2].cpu().numpy()
+    d0 = r.diagrams.numpy("d0")
+    d2 = r.diagrams.numpy("d2")
+    assert len(p) == len(c1) - len(d0) == len(c2) - len(d2)
+    births = np.setdiff1d(c1, d0["death_id"])
+    deaths = np.setdiff1d(c2, d2["birth_id"])
+    assert np.array_equal(np.sort(p["birth_id"]), births)
+    assert np.array_equal(p["death_id"], deaths)  # listed by increasing triangle id
+    fl = f.cpu().numpy().reshape(-1)
+    order = r.order.cpu().numpy().reshape(-1)
+    assert np.array_equal(p["birth"].view(np.uint32), fl[p["birth_vtx"]].view(np.uint32))
+    assert np.array_equal(p["death"].view(np.uint32), fl[p["death_vtx"]].view(np.uint32))
+    assert np.all(order[p["death_vtx"]] >= order[p["birth_vtx"]])

@@ -457,109 +457,6 @@ __global__ void __launch_bounds__(256) advance(Grid g, const uint32_t* __restric
   }
 }
 
-// The same round with one warp per column, for the last rounds, where few
-// columns are left but their boundaries are large: lane 0 runs the column
-// (expansions are sequential), and the whole warp adds an earlier column's
-// boundary -- a parallel copy of its heap behind this one's, then Floyd's
-// bottom-up heap construction level by level (the sift-downs of one level
-// touch disjoint subtrees).
-__device__ __forceinline__ void sift_down(HEnt* h, uint32_t n, uint32_t i) {
-  const HEnt x = h[i];
-  for (;;) {
-    uint32_t l = 2 * i + 1;
-    if (l >= n) break;
-    if (l + 1 < n && h[l + 1].key > h[l].key) ++l;
-    if (h[l].key <= x.key) break;
-    h[i] = h[l];
-    i = l;
-  }
-  h[i] = x;
-}
-
-__global__ void __launch_bounds__(256) advance_warp(Grid g, const uint32_t* __restrict__ order,
-                                                    const uint64_t* __restrict__ rec,
-                                                    const int64_t* __restrict__ crit1, int64_t n1,
-                                                    int64_t n2, D1Ws w, int64_t limit,
-                                                    int32_t* dstatus) {
-  const unsigned FULL = 0xFFFFFFFFu;
-  const int lane = threadIdx.x & 31;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; j < n2; j += nwarps) {
-    Col c = w.col[j];  // every lane reads it; lane 0's copy is the one kept
-    if (c.state != 1 || w.settled[j]) continue;
-    int64_t steps = 0;
-    for (;;) {
-      int act = 0;  // 1: add column oc's boundary
-      uint32_t oc = 0;
-      if (lane == 0) {
-        if (c.pivot != kNone || expand_col(g, order, rec, crit1, n1, w, c, steps, limit, dstatus)) {
-          const unsigned long long o = w.owner_key[c.pivot];
-          if (o > c.key) {
-            atomicMin(w.owner_key + c.pivot, c.key);
-          } else if (o < c.key) {
-            oc = w.owner_col[c.pivot];
-            if (oc < (uint64_t)n2 && w.settled[oc]) {
-              const Col oo = w.col[oc];
-              act = (oo.key == o && oo.pivot == c.pivot) ? 1 : 0;
-            }
-          }
-        }
-      }
-      act = __shfl_sync(FULL, act, 0);
-      if (!act) break;
-      oc = __shfl_sync(FULL, oc, 0);
-      const Col oo = w.col[oc];
-      // room: lane 0 takes a larger segment when needed, all lanes copy
-      unsigned long long off = c.off, noff = 0;
-      uint32_t size = c.size, cap = c.cap, ncap = 0;
-      int ok = 1;
-      if (lane == 0 && (uint64_t)size + oo.size > cap) {
-        const uint64_t want = std::max<uint64_t>(2ull * cap, (uint64_t)size + oo.size);
-        ok = want <= 0xFFFFFFFFull;
-        if (ok) {
-          noff = atomicAdd(w.ctr + 0, (unsigned long long)want);
-          ok = noff + want <= (unsigned long long)w.pool_cap;
-          ncap = (uint32_t)want;
-        }
-      }
-      ok = __shfl_sync(FULL, ok, 0);
-      if (!ok) {
-        if (lane == 0) fail(w, c, dstatus, DMS_ERR_CAPACITY);
-        break;
-      }
-      off = __shfl_sync(FULL, off, 0);
-      size = __shfl_sync(FULL, size, 0);
-      cap = __shfl_sync(FULL, cap, 0);
-      noff = __shfl_sync(FULL, noff, 0);
-      ncap = __shfl_sync(FULL, ncap, 0);
-      if (ncap) {
-        for (uint32_t i = lane; i < size; i += 32) w.pool[noff + i] = w.pool[off + i];
-        off = noff;
-        cap = ncap;
-      }
-      HEnt* h = w.pool + off;
-      const HEnt* src = w.pool + oo.off;
-      for (uint32_t i = lane; i < oo.size; i += 32) h[size + i] = src[i];
-      __syncwarp();
-      const uint32_t n = size + oo.size;
-      // Floyd: the internal nodes [0, n/2), deepest level first
-      int top = 31 - __clz((int)max(n / 2, 1u));  // level of node n/2 - 1
-      for (int lvl = top; lvl >= 0; --lvl) {
-        const uint32_t lo = (1u << lvl) - 1u, hi = min((2u << lvl) - 1u, n / 2);
-        for (uint32_t i = lo + lane; i < hi; i += 32) sift_down(h, n, i);
-        __syncwarp();
-      }
-      if (lane == 0) {
-        c.off = off;
-        c.cap = cap;
-        c.size = n;
-        c.pivot = kNone;
-      }
-    }
-    if (lane == 0) w.col[j] = c;
-  }
-}
-
 // each pivot's earliest claimant settles on it; counts the unsettled columns
 __global__ void publish(int64_t n2, D1Ws w) {
   unsigned long long unsettled = 0;
@@ -660,7 +557,6 @@ __global__ void init_state(Col* col, int64_t n2) {
 constexpr uint32_t kCap0 = 16;        // first heap segment of every column
 constexpr int kMaxRounds = 4096;      // reduction rounds before DMS_ERR_TIMEOUT
 constexpr int64_t kExpandLimit = 1ll << 26;  // heap pops of one column in one round
-constexpr int64_t kWarpTail = 32768;  // unsettled columns below which a warp takes each
 
 }  // namespace
 
@@ -703,24 +599,16 @@ int launch_d1(const float* f, const uint32_t* order, const uint64_t* rec, const 
   DMS_CUDA_OK(cudaMemcpyAsync(w.ctr + 0, &cursor0, sizeof(cursor0), cudaMemcpyHostToDevice, s));
   init_cols<<<nb(n2), TB, 0, s>>>(g, order, crit2, n2, w, kCap0, dstatus); count_launch();
   DMS_CUDA_OK(cudaMemsetAsync(w.settled, 0, std::max<int64_t>(n2, 1), s));
-  unsigned long long unsettled = ~0ull;
   for (int round = 1;; ++round) {
     if (round > kMaxRounds) return DMS_ERR_TIMEOUT;
     DMS_CUDA_OK(cudaMemsetAsync(w.ctr + 1, 0, 2 * sizeof(unsigned long long), s));
-    if (unsettled > (unsigned long long)kWarpTail) {
-      advance<<<nb(n2), TB, 0, s>>>(g, order, rec, crit1, n1, n2, w, kExpandLimit, dstatus); count_launch();
-    } else {  // few columns left: a warp for each
-      // warps stride over all columns and skip the settled ones
-      const unsigned wb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n2 * 32 + TB - 1) / TB, 1 << 16));
-      advance_warp<<<wb, TB, 0, s>>>(g, order, rec, crit1, n1, n2, w, kExpandLimit, dstatus); count_launch();
-    }
+    advance<<<nb(n2), TB, 0, s>>>(g, order, rec, crit1, n1, n2, w, kExpandLimit, dstatus); count_launch();
     publish<<<nb(n2), TB, 0, s>>>(n2, w); count_launch();
     unsigned long long h[2] = {0, 0};
     DMS_CUDA_OK(cudaMemcpyAsync(h, w.ctr + 1, sizeof(h), cudaMemcpyDeviceToHost, s));
     DMS_CUDA_OK(cudaStreamSynchronize(s));
     if (h[1]) break;  // a column failed: its status bit is set
     if (h[0] == 0) break;
-    unsettled = h[0];
   }
   const int64_t ntiles = (n2 + WTILE - 1) / WTILE;
   count_out<<<(unsigned)ntiles, WNT, 0, s>>>(n2, w); count_launch();

@@ -249,6 +249,48 @@ def diagram_from_host(field_host, device="cuda"):
             res.diagrams.numpy("d0_essential"))
 
 
+def diagrams_from_host(fields_host, device="cuda"):
+    """End-to-end for a sequence of fields in host memory (page-locked for
+    the copies to overlap): yields, per field, its D0 / D2 pairs and
+    essential class as numpy structured arrays, like diagram_from_host.
+    The host-to-device copy of the next field runs on a separate stream
+    while the current field goes through the path, into the second of two
+    device buffers, so the copies hide behind the compute."""
+    dev = torch.device(device)
+    compute = torch.cuda.current_stream(dev)
+    copier = torch.cuda.Stream(dev)
+    bufs, ready = [None, None], [None, None]
+
+    def enqueue(i, x):
+        if not isinstance(x, torch.Tensor):
+            x = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32))
+        if bufs[i] is None or bufs[i].shape != x.shape:
+            bufs[i] = torch.empty(x.shape, dtype=torch.float32, device=dev)
+        copier.wait_stream(compute)  # the buffer's last reader is done
+        with torch.cuda.stream(copier):
+            bufs[i].copy_(x, non_blocking=True)
+            ready[i] = torch.cuda.Event()
+            ready[i].record(copier)
+
+    it = iter(fields_host)
+    nxt = next(it, None)
+    if nxt is None:
+        return
+    cur = 0
+    enqueue(cur, nxt)
+    while True:
+        compute.wait_event(ready[cur])
+        nxt = next(it, None)
+        if nxt is not None:
+            enqueue(1 - cur, nxt)  # overlaps the path below
+        res = diagram(bufs[cur])
+        yield (res.diagrams.numpy("d0"), res.diagrams.numpy("d2"),
+               res.diagrams.numpy("d0_essential"))
+        if nxt is None:
+            return
+        cur = 1 - cur
+
+
 # ------------------------------------------------------------------ diff --
 
 def pair_values(pairs: torch.Tensor) -> torch.Tensor:

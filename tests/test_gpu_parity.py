@@ -157,3 +157,21 @@ def test_parity_structured_fields():
         _check_all(np.ascontiguousarray(f))
     r = oracle.run(const)
     assert [len(r.crit(d)) for d in range(4)] == [1, 0, 0, 0]
+
+
+def test_stream_of_host_fields_matches_one_by_one():
+    """diagrams_from_host (the next field's copy overlapped with the current
+    field's path, two device buffers) gives each field the pairs it gets
+    alone, also when shapes change along the stream."""
+    xs = [fields.gaussian_mixture((20, 21, 22), 5, (0.1, 0.3), 1e-3, s).numpy() for s in range(3)]
+    xs.append(np.random.default_rng(4).random((9, 30, 17)).astype(np.float32))
+    hosts = [torch.from_numpy(x).pin_memory() for x in xs]
+    got = list(dms.diagrams_from_host(hosts))
+    assert len(got) == len(xs)
+    for (d0, d2, ess), x in zip(got, xs):
+        r = oracle.run(x)
+        for mine, ref, key in ((d0, oracle.D0, "death_id"), (d2, oracle.D2, "birth_id")):
+            b = r.get(ref)
+            b = b[np.argsort(b[key], kind="stable")]
+            assert mine.tobytes() == b.tobytes()
+        assert ess["birth_id"][0] == r.get(oracle.D0_ESSENTIAL)["birth_id"][0]

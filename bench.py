@@ -441,7 +441,10 @@ def main():
     if args.leg:
         legs = {"batched": bench_batched, "diff": bench_differentiable, "2d": bench_2d,
                 "d1": bench_d1}
-        out = legs[args.leg](dev, args.steps, args.warmup)
+        if args.leg == "d1" and args.size:
+            out = bench_d1(dev, args.steps, args.warmup, n=args.size)
+        else:
+            out = legs[args.leg](dev, args.steps, args.warmup)
         print(json.dumps({"leg": args.leg, **out}), flush=True)
         return
 

@@ -253,14 +253,12 @@ def diagrams_from_host(fields_host, device="cuda"):
     """End-to-end for a sequence of fields in host memory (page-locked for
     the copies to overlap): yields, per field, its D0 / D2 pairs and
     essential class as numpy structured arrays, like diagram_from_host.
-    Copies hide behind the compute: the next field's host-to-device copy
-    runs on one copy stream, into the second of two device buffers, and the
-    previous field's pairs come back on another while the current field
-    goes through the path (its pairing rounds block the host, not the copy
-    engines)."""
+    The host-to-device copy of the next field runs on a separate stream
+    while the current field goes through the path, into the second of two
+    device buffers, so the copies hide behind the compute."""
     dev = torch.device(device)
     compute = torch.cuda.current_stream(dev)
-    h2d, d2h = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    copier = torch.cuda.Stream(dev)
     bufs, ready = [None, None], [None, None]
 
     def enqueue(i, x):
@@ -268,34 +266,17 @@ def diagrams_from_host(fields_host, device="cuda"):
             x = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32))
         if bufs[i] is None or bufs[i].shape != x.shape:
             bufs[i] = torch.empty(x.shape, dtype=torch.float32, device=dev)
-        h2d.wait_stream(compute)  # the buffer's last reader is done
-        with torch.cuda.stream(h2d):
+        copier.wait_stream(compute)  # the buffer's last reader is done
+        with torch.cuda.stream(copier):
             bufs[i].copy_(x, non_blocking=True)
             ready[i] = torch.cuda.Event()
-            ready[i].record(h2d)
-
-    def fetch(res):
-        d2h.wait_stream(compute)
-        with torch.cuda.stream(d2h):
-            out = []
-            for t in (res.diagrams.d0, res.diagrams.d2, res.diagrams.d0_essential):
-                h = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
-                h.copy_(t, non_blocking=True)
-                out.append(h)
-            done = torch.cuda.Event()
-            done.record(d2h)
-        return done, out, res  # res keeps the device pairs alive until copied
-
-    def arrays(pending):
-        done, out, _ = pending
-        done.synchronize()
-        return tuple(h.numpy().view(PAIR_DTYPE).reshape(-1) for h in out)
+            ready[i].record(copier)
 
     it = iter(fields_host)
     nxt = next(it, None)
     if nxt is None:
         return
-    cur, pending = 0, None
+    cur = 0
     enqueue(cur, nxt)
     while True:
         compute.wait_event(ready[cur])
@@ -303,14 +284,11 @@ def diagrams_from_host(fields_host, device="cuda"):
         if nxt is not None:
             enqueue(1 - cur, nxt)  # overlaps the path below
         res = diagram(bufs[cur])
-        fetched = fetch(res)       # overlaps the next field's path
-        if pending is not None:
-            yield arrays(pending)
-        pending = fetched
+        yield (res.diagrams.numpy("d0"), res.diagrams.numpy("d2"),
+               res.diagrams.numpy("d0_essential"))
         if nxt is None:
-            break
+            return
         cur = 1 - cur
-    yield arrays(pending)
 
 
 # ------------------------------------------------------------------ diff --

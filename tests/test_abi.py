@@ -102,3 +102,32 @@ def test_diagram_workspace_size_covers_its_parts(lib):
     assert size(10, 100_000, 100, 10) - base >= 44 * (100_000 - 100)
     assert size(10, 100, 100_000, 10) - base >= 44 * (100_000 - 100)
     assert size(50_000, 100, 100, 10) > base  # union-find nodes
+
+
+def test_d1_and_selfcorrecting_host_validation(lib):
+    """The D1 call and the self-correcting D0/D2 call answer bad arguments on
+    the host, before any launch; the D1 workspace grows with its pool."""
+    from paper_2505_21266_gb300 import _lib
+    d = _lib.dms_dims(8, 9, 10)
+    nc = (ctypes.c_int64 * 4)(5, 50, 40, 4)
+    w0 = lib.dms_diagram_d1_workspace_size(d, nc, 0)
+    assert w0 > 0
+    assert lib.dms_diagram_d1_workspace_size(d, nc, 10 * w0) > w0
+    assert lib.dms_diagram_d1_workspace_size(_lib.dms_dims(1, 9, 10), nc, 0) == 0
+    fake = ctypes.c_void_p(0x1000)
+    call = lambda dims, ncrit, d0n, cap, pool, wsb: lib.dms_diagram_d1(
+        fake, fake, fake, dims, fake, fake, ncrit, fake, d0n, fake, 0, fake, cap, fake, pool,
+        fake, wsb, fake, None)
+    assert call(_lib.dms_dims(1, 9, 10), nc, 0, 40, 0, 1 << 40) == 2   # DMS_ERR_DIMS
+    assert call(d, nc, -1, 40, 0, 1 << 40) == 8                         # negative D0 count
+    assert call(d, nc, 0, -1, 0, 1 << 40) == 8                          # negative capacity
+    assert call(d, nc, 0, 40, -5, 1 << 40) == 8                         # negative pool
+    assert call(d, nc, 0, 40, 0, 16) == 5                               # DMS_ERR_WORKSPACE
+    assert lib.dms_diagram_d1(fake, None, fake, d, fake, fake, nc, fake, 0, fake, 0, fake, 40,
+                              fake, 0, fake, 1 << 40, fake, None) == 1  # DMS_ERR_NULL
+    sc = lambda dims, ncrit: lib.dms_diagram_d0d2_selfcorrecting(
+        fake, fake, fake, fake, dims, fake, fake, fake, fake, ncrit, fake, 4, fake, 4, fake, fake,
+        fake, 16, fake, None)
+    assert sc(_lib.dms_dims(1, 9, 10), nc) == 2
+    assert sc(d, (ctypes.c_int64 * 4)(0, 50, 40, 4)) == 8                 # no minimum
+    assert sc(d, nc) == 5                                                  # workspace too small

@@ -184,12 +184,18 @@ def diagram_d0d2(field: torch.Tensor, order_t: torch.Tensor, g: Gradient, crit,
     return Diagrams(d0[: n[0]], d2[: n[1]], ess)
 
 
+# boundary-pool entries per critical triangle that the last D1 call needed
+# (the library's default is 96); later calls start from it
+_d1_pool_ratio = [96]
+
+
 def diagram_d1(field: torch.Tensor, order_t: torch.Tensor, g: Gradient, crit, dg: Diagrams,
                pool_entries: int = 0, max_tries: int = 4) -> torch.Tensor:
     """D1 pairs (birth = critical edge, death = critical triangle) of a 3D
     field after its D0 / D2 pairs (Sec. 2.5, Alg. 2 and Alg. 3), as pair
     records [n1, 32] in increasing triangle-id order.  The boundary pool
-    grows (the call is repeated) when a boundary outgrows it."""
+    grows (the call is repeated) when a boundary outgrows it, and the size
+    that worked is where the next call starts."""
     _require_cuda(field, "field", torch.float32)
     lib = _lib.load()
     dev = field.device
@@ -200,7 +206,8 @@ def diagram_d1(field: torch.Tensor, order_t: torch.Tensor, g: Gradient, crit, dg
     cap1 = max(nc[2] - n_d2, 0)
     out = torch.empty((max(cap1, 1), PAIR_BYTES), dtype=torch.uint8, device=dev)
     n_out = torch.zeros(1, dtype=torch.int64, device=dev)
-    pool = int(pool_entries)
+    ratio = _d1_pool_ratio[0]
+    pool = int(pool_entries) if pool_entries else ratio * max(nc[2], 1) + 65536
     for _ in range(max_tries):
         ws = _ws(lib.dms_diagram_d1_workspace_size(d, ncarr, pool), dev)
         st = torch.zeros(1, dtype=torch.int32, device=dev)
@@ -212,10 +219,13 @@ def diagram_d1(field: torch.Tensor, order_t: torch.Tensor, g: Gradient, crit, dg
                                   _ptr(n_out), pool, _ptr(ws), ws.numel(), _ptr(st),
                                   _stream(dev)), "dms_diagram_d1")
         v = int(st.item())
-        if v == (1 << 4) and pool >= 0:  # the pool only: retry with four times as much
-            pool = 4 * (pool or 96 * max(nc[2], 1) + 65536)
+        if v == (1 << 4):  # the pool only: retry with four times as much
+            pool *= 4
+            ratio *= 4
             continue
         _device_status_check(st, "dms_diagram_d1")
+        if not pool_entries:
+            _d1_pool_ratio[0] = ratio
         return out[: int(n_out.item())]
     raise DMSError(4, "dms_diagram_d1")
 

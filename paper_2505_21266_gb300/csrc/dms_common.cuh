@@ -53,6 +53,13 @@ struct WsCarver {
     if (e_ != cudaSuccess) return DMS_ERR_CUDA; \
   } while (0)
 
+// propagate a non-zero library status
+#define DMS_TRY(call)                 \
+  do {                                \
+    const int st_ = (call);           \
+    if (st_ != DMS_OK) return st_;    \
+  } while (0)
+
 // number of kernels this library has launched (instrumentation for the
 // benchmark's launch count; defined in dms_capi.cu)
 long long& launch_counter();

@@ -1,6 +1,7 @@
 // Extremum-saddle persistence pairs D0 and D2 (Sec. 2.5, Alg. 1; Sec. 4.1-4.2).
 //
-// 1. v-path tracing, one thread per critical saddle.  D0: from both vertices
+// 1. v-path tracing, two walks per critical saddle, dealt to the lanes of a
+//    persistent grid as their previous walks end.  D0: from both vertices
 //    of a critical edge, follow desc[] (vertex -> paired edge -> other vertex)
 //    to a minimum.  D2: from both cofacets of a critical triangle follow the
 //    dual gradient (tet -> its paired facet -> that facet's other cofacet) to
@@ -445,7 +446,7 @@ struct DualWalk {
     fields.coords(st.g, a - off, ax, ay, az);
     int64_t cof[2];
     tri_cofacets(st.g, a, k, ax, ay, az, cof);
-    const int64_t t = cof[j];
+    const int64_t t = j ? cof[1] : cof[0];
     if (t < 0) {
       r = 0;  // no cofacet on that side: the walk starts OUTSIDE
       return false;
@@ -495,26 +496,90 @@ struct DualWalk {
   }
 };
 
-// Both walks of every saddle, one thread per saddle (grid-stride when the
-// count is on the device).  The walks are chains of dependent loads; many
-// resident warps hide their latency, and path sharing keeps them short.
+// Both walks of every saddle, taken from a queue by the lanes of a
+// persistent grid: a lane whose walk has ended takes the next walk id, so
+// that one long walk no longer holds the other 31 lanes of its warp idle
+// (with a saddle per thread, 5-6 lanes of 32 were active on average).  The
+// walks are chains of dependent loads, and the number in flight is what
+// hides their latency.  A warp takes ids from the shared cursor in blocks of
+// kWalkBlock (one atomic per block, not per walk) and deals them out to its
+// lanes in order.  Walk w is walk w & 1 of saddle w >> 1; the walks of one
+// saddle may run at the same time, which the claims allow (see above).
+constexpr uint32_t kWalkBlock = 256;
+
+__device__ __forceinline__ void store_walk(Tri T, uint32_t w, uint32_t r) {
+  if (w & 1) T.s[w >> 1].rb = r;
+  else T.s[w >> 1].ra = r;
+}
+
 template <class W>
-__global__ void __launch_bounds__(256) walk_each(const W wk, const int64_t* n_dev, int64_t n_host,
-                                                 Tri T, int32_t* dstatus) {
+__global__ void __launch_bounds__(256) walk_queue(const W wk, const int64_t* n_dev, int64_t n_host,
+                                                  unsigned int* cursor, Tri T, int32_t* dstatus) {
   const int64_t ns = n_dev ? *n_dev : n_host;
-  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < ns;
-       s += (int64_t)gridDim.x * blockDim.x) {
-#pragma unroll 1
-    for (int j = 0; j < 2; ++j) {
-      typename W::State st;
-      uint32_t r = 0;
-      if (wk.start(s, j, st, r))
-        while (wk.step(st, (uint32_t)(2 * s + j), r, dstatus)) {
+  const uint32_t nwalks = (uint32_t)(2 * ns);  // < 2^31: walk ids sit below kLinkBit
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  uint32_t qnext = 0, qend = 0;  // this warp's block of walk ids (warp-uniform)
+  uint32_t cur = kNone;          // the lane's walk, kNone between walks
+  bool done = false;             // no walk left for this lane
+  typename W::State st;
+  for (;;) {
+    const bool need = !done && cur == kNone;
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, need);
+    if (m) {
+      const uint32_t k = (uint32_t)__popc(m), i = (uint32_t)__popc(m & lt);
+      uint32_t nbase = 0;
+      if (qnext + k > qend) {  // the block runs out: take the next one
+        if (lane == 0) nbase = atomicAdd(cursor, kWalkBlock);
+        nbase = __shfl_sync(0xFFFFFFFFu, nbase, 0);
+      }
+      if (need) {
+        const uint32_t w = qnext + i < qend ? qnext + i : nbase + (qnext + i - qend);
+        if (w < nwalks) {
+          uint32_t r = 0;
+          if (wk.start((int64_t)(w >> 1), (int)(w & 1), st, r)) cur = w;
+          else store_walk(T, w, r);
+        } else {
+          done = true;
         }
-      if (j) T.s[s].rb = r;
-      else T.s[s].ra = r;
+      }
+      if (qnext + k > qend) {
+        qnext = nbase + (qnext + k - qend);
+        qend = nbase + kWalkBlock;
+      } else {
+        qnext += k;
+      }
     }
+    if (cur != kNone) {
+      uint32_t r = 0;
+      if (!wk.step(st, cur, r, dstatus)) {
+        store_walk(T, cur, r);
+        cur = kNone;
+      }
+    }
+    if (__all_sync(0xFFFFFFFFu, done)) break;
   }
+}
+
+// the walks of n saddles (count on the device when n_dev is given); cursor
+// is a zeroed device word
+template <class W>
+int launch_walks(const W& wk, const int64_t* n_dev, int64_t n_host, unsigned int* cursor, Tri T,
+                 int32_t* dstatus, cudaStream_t s) {
+  static int blocks = 0;
+  if (blocks == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_queue<W>, 256, 0) !=
+            cudaSuccess)
+      return DMS_ERR_CUDA;
+    blocks = std::max(1, sms * std::max(1, per_sm));
+  }
+  unsigned g = (unsigned)blocks;
+  if (!n_dev) g = (unsigned)std::min<int64_t>(g, (2 * n_host + 255) / 256 + 1);
+  walk_queue<<<g, 256, 0, s>>>(wk, n_dev, n_host, cursor, T, dstatus); count_launch();
+  return DMS_OK;
 }
 
 // Second pass (D0 and D2): resolve both walks of each saddle to their end
@@ -869,7 +934,7 @@ struct DiagWs {
   Tri T0, T2;
   uint32_t *live0, *live1;
   uint32_t* forest;  // the spanning-forest saddles found by the Borůvka rounds
-  unsigned int* ctr;  // [0..1] live counts, [2] forest count
+  unsigned int* ctr;  // [0..1] live counts, [2] forest count, [3] changed, [4] finish count, [6] walk cursor
   Nodes nd;  // union-find nodes: parent, best live saddle, age
   // the self-correcting pairing's next links (the current ones live in
   // nd.parent and nd.best)
@@ -1159,7 +1224,7 @@ int launch_diagram(const float* f, const uint32_t* order, const uint8_t* desc, c
     mark_ends<<<nb(nc[0]), TB, 0, s>>>(crit0, nullptr, nc[0], 0, w.claim); count_launch();
     d0_weights<<<nb(nc[1]), TB, 0, s>>>(D, order, crit1, nc[1], w.T0); count_launch();
     const DescWalk<OneField> wk{OneField{g}, crit1, desc, w.claim};
-    walk_each<<<nb(nc[1]), TB, 0, s>>>(wk, nullptr, nc[1], w.T0, dstatus); count_launch();
+    DMS_TRY(launch_walks(wk, nullptr, nc[1], w.ctr + 6, w.T0, dstatus, s));
     link_walks<<<nb(nc[1]), TB, 0, s>>>(nc[1], w.T0, w.live0, w.ctr + 0, dstatus); count_launch();
   }
   w.nd.immortal = kNone;  // every minimum but the global one can die
@@ -1179,7 +1244,7 @@ int launch_diagram(const float* f, const uint32_t* order, const uint8_t* desc, c
     }
     d2_weights<<<nb(nc[2]), TB, 0, s>>>(D, order, crit2, nc[2], w.T2); count_launch();
     const DualWalk<OneField> wk{OneField{g}, crit2, rec, w.claim};
-    walk_each<<<nb(nc[2]), TB, 0, s>>>(wk, nullptr, nc[2], w.T2, dstatus); count_launch();
+    DMS_TRY(launch_walks(wk, nullptr, nc[2], w.ctr + 6, w.T2, dstatus, s));
     link_walks<<<nb(nc[2]), TB, 0, s>>>(nc[2], w.T2, w.live0, w.ctr + 0, dstatus); count_launch();
   }
   w.nd.immortal = 0;  // OUTSIDE
@@ -1681,7 +1746,7 @@ int launch_diagram_batch(const float* f, const uint32_t* order, const uint8_t* d
   b_d0_weights<<<G, TB, 0, s>>>(ft, order, crit[1], cnt_dev, w.T0); count_launch();
   {
     const DescWalk<ManyFields> wk{ManyFields{fields_dev, nfields}, crit[1], desc, w.claim};
-    walk_each<<<G * 2, TB, 0, s>>>(wk, cnt_dev + 1, 0, w.T0, dstatus); count_launch();
+    DMS_TRY(launch_walks(wk, cnt_dev + 1, 0, w.ctr + 6, w.T0, dstatus, s));
   }
   b_link_walks<<<G, TB, 0, s>>>(cnt_dev + 1, w.T0, w.live0, w.ctr + 0, dstatus); count_launch();
   w.nd.immortal = kNone;
@@ -1696,7 +1761,7 @@ int launch_diagram_batch(const float* f, const uint32_t* order, const uint8_t* d
   b_d2_weights<<<G, TB, 0, s>>>(ft, order, crit[2], cnt_dev, w.T2); count_launch();
   {
     const DualWalk<ManyFields> wk{ManyFields{fields_dev, nfields}, crit[2], rec, w.claim};
-    walk_each<<<G * 2, TB, 0, s>>>(wk, cnt_dev + 2, 0, w.T2, dstatus); count_launch();
+    DMS_TRY(launch_walks(wk, cnt_dev + 2, 0, w.ctr + 6, w.T2, dstatus, s));
   }
   b_link_walks<<<G, TB, 0, s>>>(cnt_dev + 2, w.T2, w.live0, w.ctr + 0, dstatus); count_launch();
   w.nd.immortal = 0;  // OUTSIDE, shared by all fields
@@ -2072,7 +2137,7 @@ int launch_diagram2d(const float* f, const uint32_t* order, const uint8_t* desc,
     mark_ends<<<nb(nc[0]), TB, 0, s>>>(crit0, nullptr, nc[0], 0, w.claim); count_launch();
     d0_weights2d<<<nb(ne), TB, 0, s>>>(g, order, crit1, ne, w.T0); count_launch();
     const DescWalk2d wk{g, crit1, desc, w.claim};
-    walk_each<<<nb(ne), TB, 0, s>>>(wk, nullptr, ne, w.T0, dstatus); count_launch();
+    DMS_TRY(launch_walks(wk, nullptr, ne, w.ctr + 6, w.T0, dstatus, s));
     link_walks<<<nb(ne), TB, 0, s>>>(ne, w.T0, w.live0, w.ctr + 0, dstatus); count_launch();
   }
   w.nd.immortal = kNone;
@@ -2091,7 +2156,7 @@ int launch_diagram2d(const float* f, const uint32_t* order, const uint8_t* desc,
     }
     d1_weights2d<<<nb(ne), TB, 0, s>>>(g, order, crit1, ne, w.T0); count_launch();
     const DualWalk2d wk{g, crit1, rec, w.claim};
-    walk_each<<<nb(ne), TB, 0, s>>>(wk, nullptr, ne, w.T0, dstatus); count_launch();
+    DMS_TRY(launch_walks(wk, nullptr, ne, w.ctr + 6, w.T0, dstatus, s));
     link_walks<<<nb(ne), TB, 0, s>>>(ne, w.T0, w.live0, w.ctr + 0, dstatus, true); count_launch();
   }
   w.nd.immortal = 0;  // OUTSIDE

@@ -341,14 +341,21 @@ int launch_single(const uint32_t* order, const Grid& g, uint8_t* desc, uint64_t*
       return DMS_ERR_CUDA;
     configured = true;
   }
-  int dev = 0, sms = 148;
+  int dev = 0, sms = 148, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gradient_kernel<TY>, NT, smem) !=
+          cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
   const int64_t tx = (g.nx + TX - 1) / TX, ty = (g.ny + TY - 1) / TY;
-  // z chunks: enough CTAs for several waves, chunks of at least 8 slabs
-  int64_t want = (int64_t)sms * 8;
+  // z chunks: about 16 waves of resident CTAs, so that the last, partly
+  // filled wave costs little (at 1024^3 the x-y tiles alone make 2.3 waves,
+  // and the third ran a quarter full), in chunks of at least 32 slabs (each
+  // chunk also computes the slab above it)
+  const int64_t want = (int64_t)sms * per_sm * 16;
   int64_t nzc = (want + tx * ty - 1) / (tx * ty);
-  nzc = std::max<int64_t>(1, std::min<int64_t>(nzc, (g.nz + 7) / 8));
+  nzc = std::max<int64_t>(1, std::min<int64_t>(nzc, g.nz / 32));
   int zc = (int)((g.nz + nzc - 1) / nzc);
   nzc = (g.nz + zc - 1) / zc;
   if (cudaMemsetAsync(crit_counts, 0, 4 * sizeof(int64_t), s) != cudaSuccess) return DMS_ERR_CUDA;

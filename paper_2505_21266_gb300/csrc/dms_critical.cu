@@ -12,8 +12,8 @@
 namespace dms {
 namespace {
 
-constexpr int CNT = 256;
-constexpr int CITEMS = 16;
+constexpr int CNT = 512;
+constexpr int CITEMS = 8;
 constexpr int CTILE = CNT * CITEMS;
 
 constexpr uint64_t kEdgeLsb = 0x49249ull;
@@ -91,6 +91,31 @@ __global__ void __launch_bounds__(CNT) count_kernel(const uint8_t* __restrict__ 
   }
 }
 
+// the critical ids of one anchor a (record r, desc d), in type order, to
+// put(dim, id); set bits are visited by find-first-set, not tested one by one
+template <class Put>
+__device__ __forceinline__ void anchor_ids(int64_t a, uint8_t d, uint64_t r, Put&& put) {
+  if (d == 15) put(0, a);
+  if (!r) return;
+  for (uint64_t m = r & (r >> 1) & (r >> 2) & kEdgeLsb; m; m &= m - 1)
+    put(1, 7 * a + (__ffsll((long long)m) - 1) / 3);
+  for (uint64_t m = r & kTriMask; m; m &= m - 1)
+    put(2, 12 * a + (__ffsll((long long)m) - 1 - 21));
+  for (uint64_t m = r & (r >> 1) & (r >> 2) & kTetLsb; m; m &= m - 1)
+    put(3, 6 * a + (__ffsll((long long)m) - 1 - 33) / 3);
+}
+
+// Ids are staged in shared memory in list order and written out coalesced,
+// list by list; a tile with more critical simplices than the staging space
+// holds (CTILE ids; over half of that on the noisiest fields) writes them
+// directly.
+constexpr int STAGE = CTILE;
+struct WriteSmem {
+  TileSmem t;
+  long long stg[STAGE];
+  long long tcount[4], sbase[4], gbase[4];
+};
+
 __global__ void __launch_bounds__(CNT) write_kernel(const uint8_t* __restrict__ desc,
                                                     const uint64_t* __restrict__ rec, int64_t n,
                                                     int64_t ntiles,
@@ -98,47 +123,60 @@ __global__ void __launch_bounds__(CNT) write_kernel(const uint8_t* __restrict__ 
                                                     int64_t* c0, int64_t* c1, int64_t* c2,
                                                     int64_t* c3, int64_t cap0, int64_t cap1,
                                                     int64_t cap2, int64_t cap3) {
-  __shared__ TileSmem sm;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  WriteSmem& ws = *reinterpret_cast<WriteSmem*>(smem_raw);
+  TileSmem& sm = ws.t;
+  long long* const stg = ws.stg;
+  long long* const tcount = ws.tcount;
+  long long* const sbase = ws.sbase;
+  long long* const gbase = ws.gbase;
   const int64_t a0 = (int64_t)blockIdx.x * CTILE;
   stage(sm, desc, rec, a0, n);
   int tot[4] = {0, 0, 0, 0};
   for (int k = 0; k < CITEMS; ++k) {
-    int i = threadIdx.x * CITEMS + k;
+    const int i = threadIdx.x * CITEMS + k;
     int c[4];
     anchor_counts(sm.desc[padded(i)], sm.rec[padded(i)], c);
     if (a0 + i >= n) c[0] = 0;
     for (int d = 0; d < 4; ++d) tot[d] += c[d];
   }
-  long long off[4];
+  long long loc[4];
   for (int d = 0; d < 4; ++d) {
-    long long e = scan64::block_excl(tot[d], sm.tmp, nullptr);
-    off[d] = e + (boff[d * ntiles + blockIdx.x] - boff[d * ntiles]);
+    long long t;
+    loc[d] = scan64::block_excl(tot[d], sm.tmp, &t);
+    if (threadIdx.x == 0) tcount[d] = t;
   }
-  for (int k = 0; k < CITEMS; ++k) {
-    int i = threadIdx.x * CITEMS + k;
-    int64_t a = a0 + i;
-    if (a >= n) break;
-    uint64_t r = sm.rec[padded(i)];
-    if (sm.desc[padded(i)] == 15) {
-      if (off[0] < cap0) c0[off[0]] = a;
-      ++off[0];
+  if (threadIdx.x == 0) {
+    long long acc = 0;
+    for (int d = 0; d < 4; ++d) {
+      sbase[d] = acc;
+      acc += tcount[d];
+      gbase[d] = boff[d * ntiles + blockIdx.x] - boff[d * ntiles];
     }
-    if (!r) continue;
-    for (int t = 0; t < 7; ++t)
-      if (((r >> (3 * t)) & 7ull) == 7ull) {
-        if (off[1] < cap1) c1[off[1]] = 7 * a + t;
-        ++off[1];
-      }
-    for (int t = 0; t < 12; ++t)
-      if ((r >> (21 + t)) & 1ull) {
-        if (off[2] < cap2) c2[off[2]] = 12 * a + t;
-        ++off[2];
-      }
-    for (int t = 0; t < 6; ++t)
-      if (((r >> (33 + 3 * t)) & 7ull) == 7ull) {
-        if (off[3] < cap3) c3[off[3]] = 6 * a + t;
-        ++off[3];
-      }
+  }
+  __syncthreads();
+  const bool fits = sbase[3] + tcount[3] <= (long long)STAGE;
+  long long p[4];
+  for (int d = 0; d < 4; ++d) p[d] = (fits ? sbase[d] : gbase[d]) + loc[d];
+  int64_t* const lists[4] = {c0, c1, c2, c3};
+  const int64_t caps[4] = {cap0, cap1, cap2, cap3};
+  for (int k = 0; k < CITEMS; ++k) {
+    const int i = threadIdx.x * CITEMS + k;
+    const int64_t a = a0 + i;
+    if (a >= n) break;
+    anchor_ids(a, sm.desc[padded(i)], sm.rec[padded(i)], [&](int d, int64_t id) {
+      if (fits) stg[p[d]] = id;
+      else if (p[d] < caps[d]) lists[d][p[d]] = id;
+      ++p[d];
+    });
+  }
+  if (!fits) return;
+  __syncthreads();
+  for (int d = 0; d < 4; ++d) {
+    int64_t* out = lists[d];
+    const long long g0 = gbase[d], s0 = sbase[d], cnt = tcount[d];
+    for (long long j = threadIdx.x; j < cnt; j += CNT)
+      if (g0 + j < caps[d]) out[g0 + j] = stg[s0 + j];
   }
 }
 
@@ -173,7 +211,14 @@ int launch_critical(const uint8_t* desc, const uint64_t* rec, const Grid& g, int
   long long* sums = c.take<long long>(scan64::num_sums(m) + 1);
   count_kernel<<<(unsigned)ntiles, CNT, 0, s>>>(desc, rec, g.n, ntiles, bc); count_launch();
   scan64::run(bc, m, sums, s);
-  write_kernel<<<(unsigned)ntiles, CNT, 0, s>>>(desc, rec, g.n, ntiles, bc, c0, c1, c2, c3, cap[0],
+  static bool configured = false;
+  if (!configured) {
+    if (cudaFuncSetAttribute(write_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(WriteSmem)) != cudaSuccess)
+      return DMS_ERR_CUDA;
+    configured = true;
+  }
+  write_kernel<<<(unsigned)ntiles, CNT, sizeof(WriteSmem), s>>>(desc, rec, g.n, ntiles, bc, c0, c1, c2, c3, cap[0],
                                                 cap[1], cap[2], cap[3]); count_launch();
   finish_kernel<<<1, 32, 0, s>>>(bc, sums + scan64::num_sums(m), ntiles, counts, cap[0], cap[1],
                                  cap[2], cap[3], dstatus); count_launch();

@@ -585,10 +585,16 @@ int launch_walks(const W& wk, const int64_t* n_dev, int64_t n_host, unsigned int
 // Second pass (D0 and D2): resolve both walks of each saddle to their end
 // nodes; a saddle whose walks end at different nodes is live in the pairing.
 // (saddles marked in Sad::pad are left out of the pairing: on 2D grids the
-// D1 pass skips the edges D0 already paired)
+// D1 pass skips the edges D0 already paired).  With tag set it also does the
+// first round's search of the pairing rounds (round_find, round 1: every
+// node is still its own root): it records both ends as the roots and tags
+// them with the saddle, so that the rounds start at their merge step.  (A
+// resolver reading ra / rb of a saddle while it is overwritten gets the
+// walk's end node either way.)
 __global__ void __launch_bounds__(256) link_walks(int64_t nt, Tri T, uint32_t* live,
                                                   unsigned int* live_n, int32_t* dstatus,
-                                                  bool skip_marked = false) {
+                                                  bool skip_marked = false, bool tag = false,
+                                                  Nodes nd = Nodes{}) {
   __shared__ CtaAppend sh;
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   bool keep = false;
@@ -599,6 +605,13 @@ __global__ void __launch_bounds__(256) link_walks(int64_t nt, Tri T, uint32_t* l
       T.s[i].na = n0;
       T.s[i].nb = n1;
       keep = true;
+      if (tag) {
+        T.s[i].ra = n0;
+        T.s[i].rb = n1;
+        const unsigned long long tv = (1ull << 44) | (kMask44 - T.s[i].w);
+        if (n0 != nd.immortal) atomicMax(nd.best + n0, tv);
+        if (n1 != nd.immortal) atomicMax(nd.best + n1, tv);
+      }
     }
   }
   cta_append2(sh, keep, live, live_n, false, live, live_n, (uint32_t)i);
@@ -1019,7 +1032,8 @@ int run_rounds(DiagWs& w, Tri T, cudaStream_t s, int32_t* dstatus) {
 // Borůvka rounds over the live saddles in w.live0 (count ctr[0]) collect
 // the spanning forest's saddles; the node arrays are then reset and the
 // exact rounds pair the forest's saddles.
-int run_pairing(DiagWs& w, Tri T, int64_t nnode, cudaStream_t s, int32_t* dstatus) {
+int run_pairing(DiagWs& w, Tri T, int64_t nnode, cudaStream_t s, int32_t* dstatus,
+                bool first_found = false) {
   uint32_t* cur = w.live0;
   uint32_t* nxt = w.live1;
   unsigned int* cur_n = w.ctr + 0;
@@ -1034,7 +1048,9 @@ int run_pairing(DiagWs& w, Tri T, int64_t nnode, cudaStream_t s, int32_t* dstatu
     if (round >= 64) return DMS_ERR_TIMEOUT;  // components at least halve per round
     const unsigned int blocks = (unsigned int)std::min<int64_t>((h + 255) / 256, 1 << 16);
     DMS_CUDA_OK(cudaMemsetAsync(nxt_n, 0, sizeof(unsigned int), s));
-    round_find<<<blocks, 256, 0, s>>>(cur, cur_n, T, w.nd, round); count_launch();
+    if (round > 1 || !first_found) {  // else link_walks did round 1's search
+      round_find<<<blocks, 256, 0, s>>>(cur, cur_n, T, w.nd, round); count_launch();
+    }
     boruvka_hook<<<blocks, 256, 0, s>>>(cur, cur_n, T, w.nd, round, nxt, nxt_n, w.forest, forest_n); count_launch();
     std::swap(cur, nxt);
     std::swap(cur_n, nxt_n);
@@ -1225,11 +1241,13 @@ int launch_diagram(const float* f, const uint32_t* order, const uint8_t* desc, c
     d0_weights<<<nb(nc[1]), TB, 0, s>>>(D, order, crit1, nc[1], w.T0); count_launch();
     const DescWalk<OneField> wk{OneField{g}, crit1, desc, w.claim};
     DMS_TRY(launch_walks(wk, nullptr, nc[1], w.ctr + 6, w.T0, dstatus, s));
-    link_walks<<<nb(nc[1]), TB, 0, s>>>(nc[1], w.T0, w.live0, w.ctr + 0, dstatus); count_launch();
+    w.nd.immortal = kNone;  // every minimum but the global one can die
+    link_walks<<<nb(nc[1]), TB, 0, s>>>(nc[1], w.T0, w.live0, w.ctr + 0, dstatus, false,
+                                        pairing == 0, w.nd); count_launch();
   }
-  w.nd.immortal = kNone;  // every minimum but the global one can die
+  w.nd.immortal = kNone;
   int st = pairing == 1 ? run_selfcorrecting(w, w.T0, std::max<int64_t>(nc[0], 1), s, dstatus)
-                        : run_pairing(w, w.T0, std::max<int64_t>(nc[0], 1), s, dstatus);
+                        : run_pairing(w, w.T0, std::max<int64_t>(nc[0], 1), s, dstatus, true);
   if (st) return st;
   st = write_diagram(0, w, D, f, order, crit0, crit1, nc[1], d0, cap0, n_out + 0, dstatus, s);
   if (st) return st;
@@ -1245,11 +1263,13 @@ int launch_diagram(const float* f, const uint32_t* order, const uint8_t* desc, c
     d2_weights<<<nb(nc[2]), TB, 0, s>>>(D, order, crit2, nc[2], w.T2); count_launch();
     const DualWalk<OneField> wk{OneField{g}, crit2, rec, w.claim};
     DMS_TRY(launch_walks(wk, nullptr, nc[2], w.ctr + 6, w.T2, dstatus, s));
-    link_walks<<<nb(nc[2]), TB, 0, s>>>(nc[2], w.T2, w.live0, w.ctr + 0, dstatus); count_launch();
+    w.nd.immortal = 0;  // OUTSIDE
+    link_walks<<<nb(nc[2]), TB, 0, s>>>(nc[2], w.T2, w.live0, w.ctr + 0, dstatus, false,
+                                        pairing == 0, w.nd); count_launch();
   }
-  w.nd.immortal = 0;  // OUTSIDE
+  w.nd.immortal = 0;
   st = pairing == 1 ? run_selfcorrecting(w, w.T2, nc[3] + 1, s, dstatus)
-                    : run_pairing(w, w.T2, nc[3] + 1, s, dstatus);
+                    : run_pairing(w, w.T2, nc[3] + 1, s, dstatus, true);
   if (st) return st;
   st = write_diagram(2, w, D, f, order, crit2, crit3, nc[2], d2, cap2, n_out + 1, dstatus, s);
   if (st) return st;

@@ -192,16 +192,17 @@ DMS_HD int process_lower_star(uint32_t lm, const uint32_t (&o)[14], const Tables
   auto tet_key = [&](int q) -> uint32_t { return keys.q[q][tid]; };
 
   uint32_t C = 0;                       // classified link vertices (ranks)
+  uint32_t Cs = 0;                      // the same, as slots
   uint32_t I0 = 0, I1 = 0, I2 = 0;      // edges with a classified end
   uint32_t N0 = 0, N1 = 0, N2 = 0;      // edges with two classified ends
-  uint32_t K0 = 0, K1 = 0, K2 = 0;      // classified link edges (positions)
   uint64_t cT = 0;                      // classified link edges (star triangles)
   uint32_t Q1 = 0, Q2 = 0, Q3 = 0, cQ = 0;
   uint64_t eCode = 0, qCode0 = 0;
   uint32_t qCode1 = 0;
   uint64_t critT = 0;
-  auto classify_vertex = [&](uint32_t r) {
+  auto classify_vertex = [&](uint32_t r, int sr) {
     C |= 1u << r;
+    Cs |= 1u << sr;
     const uint32_t s0 = tb.star[r][0], s1 = tb.star[r][1], s2 = tb.star[r][2];
     N0 |= s0 & I0;
     N1 |= s1 & I1;
@@ -209,12 +210,6 @@ DMS_HD int process_lower_star(uint32_t lm, const uint32_t (&o)[14], const Tables
     I0 |= s0;
     I1 |= s1;
     I2 |= s2;
-  };
-  auto mark_pos = [&](uint32_t p) {
-    const uint32_t b = 1u << (p & 31);
-    if (p < 32) K0 |= b;
-    else if (p < 64) K1 |= b;
-    else K2 |= b;
   };
   auto classify_edge = [&](int j) {  // star triangle j = link edge
     cT |= tb.bit[j];
@@ -228,7 +223,7 @@ DMS_HD int process_lower_star(uint32_t lm, const uint32_t (&o)[14], const Tables
     else qCode1 |= code << (4 * (q - 16));
   };
 
-  classify_vertex(0);  // x is paired with the edge to delta (rank 0)
+  classify_vertex(0, delta);  // x is paired with the edge to delta (rank 0)
   for (;;) {
     // Prim: the frontier edge of smallest key classifies its unclassified end
     for (;;) {
@@ -240,8 +235,7 @@ DMS_HD int process_lower_star(uint32_t lm, const uint32_t (&o)[14], const Tables
       const int su = slot(u), sw = slot(u ^ h ^ l);
       const int j = tb.triOfSlots[su][sw];
       eCode |= (uint64_t)(tb.cofOfSlots[su][sw] + 1u) * tb.nib[su];
-      classify_vertex(u);
-      mark_pos(p);
+      classify_vertex(u, su);
       classify_edge(j);
     }
     // the component's link triangles and cycle edges
@@ -262,18 +256,20 @@ DMS_HD int process_lower_star(uint32_t lm, const uint32_t (&o)[14], const Tables
         set_tet_code(q, tb.tetCode[q][w]);
         cQ |= 1u << q;
         classify_edge(beta);
-        mark_pos(pos_of(rank(tb.triA[beta]), rank(tb.triB[beta])));
         pQ |= tb.triCof[beta] & QL & Q2 & ~Q3 & ~cQ;
       }
-      // PQzero: the smallest unclassified cycle edge or fully bounded tet
-      const uint32_t Z0 = E0 & N0 & ~K0, Z1 = E1 & N1 & ~K1, Z2 = E2 & N2 & ~K2;
+      // PQzero: the smallest unclassified cycle edge (a link edge, i.e. a
+      // lower-star triangle, with both ends classified) or fully bounded tet
+      const uint64_t Zt = lower_tris(tb, Cs) & ~cT;
       const uint32_t zQ = QL & Q3 & ~cQ;
-      if (!(Z0 | Z1 | Z2 | zQ)) break;
-      uint32_t bestE = 0xFFFFu, pe = 0;
-      if (Z0 | Z1 | Z2) {
-        pe = Z0 ? (uint32_t)ffs32(Z0) : (Z1 ? 32u + ffs32(Z1) : 64u + ffs32(Z2));
-        const uint32_t hl = tb.hlOfPos[pe];
-        bestE = (((hl >> 4) + 1) << 8) | (((hl & 15u) + 1) << 4);
+      if (!(Zt | zQ)) break;
+      uint32_t bestE = 0xFFFFu;
+      int je = 0;
+      for (uint64_t m = Zt; m; m &= m - 1) {
+        const int jj = ffs64(m);
+        const uint32_t ra = rank(tb.triA[jj]), rb = rank(tb.triB[jj]);
+        const uint32_t ke = ((umax(ra, rb) + 1) << 8) | ((umin(ra, rb) + 1) << 4);
+        if (ke < bestE) { bestE = ke; je = jj; }
       }
       uint32_t bestQ = 0xFFFFu;
       int q = 0;
@@ -283,11 +279,9 @@ DMS_HD int process_lower_star(uint32_t lm, const uint32_t (&o)[14], const Tables
         if (kq < bestQ) { bestQ = kq; q = qq; }
       }
       if (bestE < bestQ) {  // a critical link edge: a critical triangle of L
-        const uint32_t hl = tb.hlOfPos[pe];
-        const int j = tb.triOfSlots[slot(hl >> 4)][slot(hl & 15u)];
+        const int j = je;
         critT |= 1ull << j;
         classify_edge(j);
-        mark_pos(pe);
         pQ = tb.triCof[j] & QL & Q2 & ~Q3 & ~cQ;
       } else {  // a critical link triangle: a critical tet of L
         cQ |= 1u << q;
@@ -298,8 +292,9 @@ DMS_HD int process_lower_star(uint32_t lm, const uint32_t (&o)[14], const Tables
     const uint32_t rem = ((1u << k) - 1u) & ~C;
     if (!rem) break;
     const uint32_t r = (uint32_t)ffs32(rem);
-    eCode |= 7ull << (4 * slot(r));
-    classify_vertex(r);
+    const int sr = slot(r);
+    eCode |= 7ull << (4 * sr);
+    classify_vertex(r, sr);
   }
 
   static_for<0, 14>([&](auto S) {

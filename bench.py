@@ -254,6 +254,9 @@ def bench_batched(dev, steps: int, warmup: int):
     return {"workload": "256 fields, axes U{32..256}, half Gaussian mixtures (16, sigma "
                         "U[0.05,0.2]) + U[0,1e-3), half U[0,1)",
             "fields": 256, "vertices": total, "tile_variant": variant,
+            "variant": B.variant_name(variant),
+            "autotune_ms": {B.variant_name(i): round(t, 2)
+                            for i, t in enumerate((B.autotune.last or {}).get("ms", []))},
             "batched_ms": batched_ms, "batched_fields_per_s": 256 / (batched_ms / 1e3),
             "batched_vertices_per_s": total / (batched_ms / 1e3),
             "per_field_ms": per_ms, "per_field_fields_per_s": 256 / (per_ms / 1e3),

@@ -290,8 +290,11 @@ int dms_diagram_d1(const float* f, const uint32_t* order, const uint64_t* rec, d
  *   f            concatenated float32 fields (sum of the fields' sizes).
  *   fields_host  [nfields] table (host), fields_dev the same table on the
  *                device (both read during the call).
- *   tile_variant gradient tile shape, 0..dms_batch_tile_variants()-1 (32 x 24,
- *                32 x 16, 32 x 32 anchors per CTA; an autotuner picks one).
+ *   tile_variant gradient variant, 0..dms_batch_tile_variants()-1: tile shape
+ *                variant % 3 (32 x 24, 32 x 16, 32 x 32 anchors per CTA) and
+ *                lanes per vertex 1 + variant / 3 (two: the lane pair splits
+ *                the rank comparisons, link edges and tet keys of a vertex);
+ *                an autotuner picks one; all give the same results.
  *   order, desc, rec  concatenated outputs as in dms_order/dms_gradient, each
  *                field with its own local order and records.
  *   caps         host [4]: capacity, over all fields, of the critical lists

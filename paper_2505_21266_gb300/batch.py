@@ -3,8 +3,8 @@
 ``Batch`` owns every device buffer for one fixed list of field shapes, so a
 call allocates nothing and synchronises nothing: it can be captured once in a
 CUDA graph and replayed for each new batch of inputs.  ``autotune`` picks the
-gradient tile shape for a list of shapes by timing the compiled variants and
-keeps the winner in a small JSON cache.  ``per_field`` runs the same fields
+gradient variant -- tile shape and lanes per vertex -- for a list of shapes
+by timing the compiled variants and keeps the winner in a small JSON cache.  ``per_field`` runs the same fields
 one at a time through the single-field entry points (the comparison point for
 the batched path).
 """
@@ -180,10 +180,16 @@ def _key(shapes, device):
     return f"{torch.cuda.get_device_name(device)}|{len(shapes)}|{h}"
 
 
+def variant_name(v: int) -> str:
+    """The gradient variant v: anchors per CTA tile and lanes per vertex."""
+    return f"32x{(24, 16, 32)[v % 3]}, {1 + v // 3} lane(s)/vertex"
+
+
 def autotune(shapes, device="cuda", fields=None, reps: int = 3, use_cache: bool = True):
-    """Best gradient tile variant for these shapes (timed on the device with
-    CUDA events over graph replays of the whole batch); cached by device name
-    and shape list."""
+    """Best gradient variant (tile shape x lanes per vertex) for these shapes,
+    timed on the device with CUDA events over graph replays of the whole
+    batch; cached by device name and shape list.  The times of the last
+    call (ms per variant) are left in ``autotune.last``."""
     shapes = [tuple(int(v) for v in s) for s in shapes]
     key = _key(shapes, device)
     path = _cache_path()
@@ -194,6 +200,7 @@ def autotune(shapes, device="cuda", fields=None, reps: int = 3, use_cache: bool 
         except (OSError, ValueError):
             cache = {}
         if key in cache:
+            autotune.last = dict(cache[key])
             return int(cache[key]["variant"])
     times = []
     nvar = _lib.load().dms_batch_tile_variants()
@@ -213,6 +220,7 @@ def autotune(shapes, device="cuda", fields=None, reps: int = 3, use_cache: bool 
         times.append(e0.elapsed_time(e1) / reps)
         del b
     best = int(np.argmin(times))
+    autotune.last = {"variant": best, "ms": times}
     if use_cache:
         cache[key] = {"variant": best, "ms": times}
         try:
@@ -222,3 +230,6 @@ def autotune(shapes, device="cuda", fields=None, reps: int = 3, use_cache: bool 
         except OSError:
             pass
     return best
+
+
+autotune.last = None

@@ -39,7 +39,7 @@ int launch_diagram_batch(const float* f, const uint32_t* order, const uint8_t* d
 
 namespace {
 
-constexpr int kTileVariants = 3;
+constexpr int kTileVariants = 6;  // as dms_gradient.cu
 constexpr int kGradTX = 32;
 
 // vertex offsets of the fields (+ the total) for the segmented sort

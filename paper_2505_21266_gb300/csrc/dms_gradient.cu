@@ -99,10 +99,11 @@ __device__ __forceinline__ void load_tables(Smem<TY>& sm) {
 // (the +1 halo) slab by slab and writes complete records and desc.  Adds the
 // critical simplices of the written records to ncrit (per thread) and the
 // minima to sm.counts[0].  Requires sm.tb loaded, sm.recs zero.
-template <int TY>
+template <int TY, int TPV = 1>
 __device__ void gradient_tile(Smem<TY>& sm, const uint32_t* __restrict__ order, const Grid& g,
                               int x0, int y0, int64_t z0, int64_t zend, uint8_t* __restrict__ desc,
                               uint64_t* __restrict__ rec, unsigned int (&ncrit)[3]) {
+  constexpr int VPW = 32 / TPV;  // vertices per warp task
   constexpr int WX = Smem<TY>::WX;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t zlast = (zend < g.nz - 1) ? zend : g.nz - 1;  // vertex slabs [z0, zlast]
@@ -110,7 +111,7 @@ __device__ void gradient_tile(Smem<TY>& sm, const uint32_t* __restrict__ order, 
   load_slab(sm, order, g, x0, y0, z0, (int)(z0 % 3));
 
   const int nvx = TX + 1, nvy = TY + 1;
-  const int ntask = (nvx * nvy + 31) / 32;
+  const int ntask = (nvx * nvy + VPW - 1) / VPW;
   for (int64_t z = z0; z <= zlast; ++z) {
     load_slab(sm, order, g, x0, y0, z + 1, (int)((z + 1) % 3));
     __syncthreads();
@@ -164,7 +165,9 @@ __device__ void gradient_tile(Smem<TY>& sm, const uint32_t* __restrict__ order, 
     for (int i = tid; i < nvx * nvy; i += NT) sm.perm[atomicAdd(&sm.bucket[sm.kcnt[i]], 1u)] = (uint16_t)i;
     __syncthreads();
     for (int task = warp; task < ntask;) {
-      const int slot = task * 32 + lane;
+      // TPV lanes per vertex: the pair (lane & ~1, lane | 1) when TPV = 2
+      const int half = lane % TPV;
+      const int slot = task * VPW + lane / TPV;
       const int idx = slot < nvx * nvy ? sm.perm[slot] : 0;
       const int lx = idx % nvx, ly = idx / nvx;
       const int64_t x = x0 + lx, y = y0 + ly;
@@ -178,15 +181,18 @@ __device__ void gradient_tile(Smem<TY>& sm, const uint32_t* __restrict__ order, 
           o[s] = w[cy + dy][cx + dx];
         });
         uint64_t acc[8];
-        int d = lowerstar::process_lower_star<NT>(sm.lmask[idx], o, sm.tb, sm.keys, tid, acc);
+        const unsigned pmask = TPV == 1 ? 0xFFFFFFFFu : (3u << (lane & ~1));
+        int d = lowerstar::process_lower_star<NT, TPV>(sm.lmask[idx], o, sm.tb, sm.keys,
+                                                       TPV == 1 ? tid : (tid & ~1), acc, half,
+                                                       pmask);
         const bool owned = lx < TX && ly < TY && z < zend;
-        if (owned) {
+        if (owned && half == 0) {
           desc[x + g.nx * (y + g.ny * z)] = (uint8_t)d;
           if (d == 15) atomicAdd(&sm.counts[0], 1u);
         }
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-          if (!acc[c]) continue;
+          if (c % TPV != half || !acc[c]) continue;  // two lanes: alternate corners each
           const int ax = lx - (c & 1), ay = ly - ((c >> 1) & 1);
           const int64_t az = z - ((c >> 2) & 1);
           if (ax < 0 || ax >= TX || ay < 0 || ay >= TY || az < z0 || az >= zend) continue;
@@ -272,7 +278,7 @@ struct BatchTiles {
   unsigned long long* queue;
 };
 
-template <int TY>
+template <int TY, int TPV>
 __global__ void __launch_bounds__(NT, 4) gradient_batch_kernel(const uint32_t* __restrict__ order,
                                                             BatchTiles bt,
                                                             uint8_t* __restrict__ desc,
@@ -310,8 +316,8 @@ __global__ void __launch_bounds__(NT, 4) gradient_batch_kernel(const uint32_t* _
     const long long bx = local % tx, by = (local / tx) % ty, bz = local / ((long long)tx * ty);
     const int64_t z0 = bz * bt.zc;
     const int64_t zend = (z0 + bt.zc < g.nz) ? z0 + bt.zc : g.nz;
-    gradient_tile(sm, order + fd.offset, g, (int)bx * TX, (int)by * TY, z0, zend,
-                  desc + fd.offset, rec + fd.offset, ncrit);
+    gradient_tile<TY, TPV>(sm, order + fd.offset, g, (int)bx * TX, (int)by * TY, z0, zend,
+                           desc + fd.offset, rec + fd.offset, ncrit);
     add_counts(sm, ncrit, counts + 4 * lo);
   }
 }
@@ -352,10 +358,13 @@ int launch_single(const uint32_t* order, const Grid& g, uint8_t* desc, uint64_t*
   // z chunks: about 16 waves of resident CTAs, so that the last, partly
   // filled wave costs little (at 1024^3 the x-y tiles alone make 2.3 waves,
   // and the third ran a quarter full), in chunks of at least 32 slabs (each
-  // chunk also computes the slab above it)
-  const int64_t want = (int64_t)sms * per_sm * 16;
-  int64_t nzc = (want + tx * ty - 1) / (tx * ty);
+  // chunk also computes the slab above it); a grid that such chunks leave
+  // under two waves (a small field) takes chunks down to 8 slabs instead
+  const int64_t cap = (int64_t)sms * per_sm, tiles = tx * ty;
+  int64_t nzc = (16 * cap + tiles - 1) / tiles;
   nzc = std::max<int64_t>(1, std::min<int64_t>(nzc, g.nz / 32));
+  if (tiles * nzc < 2 * cap)
+    nzc = std::max<int64_t>(1, std::min<int64_t>((2 * cap + tiles - 1) / tiles, (g.nz + 7) / 8));
   int zc = (int)((g.nz + nzc - 1) / nzc);
   nzc = (g.nz + zc - 1) / zc;
   if (cudaMemsetAsync(crit_counts, 0, 4 * sizeof(int64_t), s) != cudaSuccess) return DMS_ERR_CUDA;
@@ -365,38 +374,43 @@ int launch_single(const uint32_t* order, const Grid& g, uint8_t* desc, uint64_t*
   return launch_status();
 }
 
-template <int TY>
+template <int TY, int TPV>
 int launch_batch(const uint32_t* order, const dms_field_desc* fields_dev, int nfields, int zc,
                  uint8_t* desc, uint64_t* rec, int64_t* counts, long long* tile0,
                  unsigned long long* queue, cudaStream_t s) {
   static bool configured = false;
   const size_t smem = sizeof(Smem<TY>);
   if (!configured) {
-    if (cudaFuncSetAttribute(gradient_batch_kernel<TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(gradient_batch_kernel<TY, TPV>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
       return DMS_ERR_CUDA;
     configured = true;
   }
   int dev = 0, sms = 148, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gradient_batch_kernel<TY>, NT, smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gradient_batch_kernel<TY, TPV>, NT,
+                                                    smem) !=
           cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
   DMS_CUDA_OK(cudaMemsetAsync(counts, 0, 4 * sizeof(int64_t) * nfields, s));
   batch_tiles_kernel<<<1, 32, 0, s>>>(fields_dev, nfields, TY, zc, tile0, queue); count_launch();
   BatchTiles bt{fields_dev, tile0, nfields, zc, queue};
-  gradient_batch_kernel<TY><<<(unsigned)(sms * per_sm), NT, smem, s>>>(
+  gradient_batch_kernel<TY, TPV><<<(unsigned)(sms * per_sm), NT, smem, s>>>(
       order, bt, desc, rec, reinterpret_cast<unsigned long long*>(counts)); count_launch();
   return launch_status();
 }
 
 }  // namespace
 
-// tile heights compiled for the autotuner (index = variant)
-constexpr int kTileVariants = 3;
-int gradient_tile_height(int variant) { return variant == 1 ? 16 : (variant == 2 ? 32 : 24); }
+// the batch variants the autotuner chooses from: tile height (variant % 3:
+// 24, 16, 32 anchor rows) x lanes per vertex (1 + variant / 3)
+constexpr int kTileVariants = 6;
+int gradient_tile_height(int variant) {
+  const int t = variant % 3;
+  return t == 1 ? 16 : (t == 2 ? 32 : 24);
+}
 
 int launch_gradient(const uint32_t* order, const Grid& g, uint8_t* desc, uint64_t* rec,
                     int64_t* crit_counts, cudaStream_t s) {
@@ -407,9 +421,12 @@ int launch_gradient_batch(const uint32_t* order, const dms_field_desc* fields_de
                           int variant, int zc, uint8_t* desc, uint64_t* rec, int64_t* counts,
                           long long* tile0, unsigned long long* queue, cudaStream_t s) {
   switch (variant) {
-    case 1: return launch_batch<16>(order, fields_dev, nfields, zc, desc, rec, counts, tile0, queue, s);
-    case 2: return launch_batch<32>(order, fields_dev, nfields, zc, desc, rec, counts, tile0, queue, s);
-    default: return launch_batch<24>(order, fields_dev, nfields, zc, desc, rec, counts, tile0, queue, s);
+    case 1: return launch_batch<16, 1>(order, fields_dev, nfields, zc, desc, rec, counts, tile0, queue, s);
+    case 2: return launch_batch<32, 1>(order, fields_dev, nfields, zc, desc, rec, counts, tile0, queue, s);
+    case 3: return launch_batch<24, 2>(order, fields_dev, nfields, zc, desc, rec, counts, tile0, queue, s);
+    case 4: return launch_batch<16, 2>(order, fields_dev, nfields, zc, desc, rec, counts, tile0, queue, s);
+    case 5: return launch_batch<32, 2>(order, fields_dev, nfields, zc, desc, rec, counts, tile0, queue, s);
+    default: return launch_batch<24, 1>(order, fields_dev, nfields, zc, desc, rec, counts, tile0, queue, s);
   }
 }
 

@@ -137,9 +137,17 @@ struct Keys {
 // being increasing keys; the frontier is E & INC & ~IN, INC = edges with a
 // classified end, IN = edges with two, both updated by OR-ing the positions
 // of the new vertex's pairs (tb.star).
-template <int NT>
+//
+// TPV = 2 (device only): two lanes of a warp, `half` 0 and 1 in the lane
+// pair pmask, run one vertex.  They split the rank comparisons (seven slots
+// each), the link edges and the tet keys (alternate set bits), combine them
+// by shuffles, and then both run the rest of the pass on the same data (keys
+// in the column tid of the pair, shared by both).
+template <int NT, int TPV = 1>
 DMS_HD int process_lower_star(uint32_t lm, const uint32_t (&o)[14], const Tables& tb,
-                               Keys<NT>& keys, int tid, uint64_t (&acc)[8]) {
+                               Keys<NT>& keys, int tid, uint64_t (&acc)[8], int half = 0,
+                               unsigned pmask = 0xFFFFFFFFu) {
+  static_assert(TPV == 1 || TPV == 2, "one or two lanes per vertex");
 #pragma unroll
   for (int c = 0; c < 8; ++c) acc[c] = 0;
   if (lm == 0) return 15;  // no lower edge: a minimum
@@ -148,17 +156,37 @@ DMS_HD int process_lower_star(uint32_t lm, const uint32_t (&o)[14], const Tables
   // one, so it never adds to a lower slot's rank)
   uint64_t R = 0, INV = 0;
   int delta = 0;
+  if constexpr (TPV == 1) {
 #pragma unroll
-  for (int s = 0; s < 14; ++s) {
-    uint32_t r = 0;
+    for (int s = 0; s < 14; ++s) {
+      uint32_t r = 0;
 #pragma unroll
-    for (int t = 0; t < 14; ++t)
-      if (t != s) r += o[t] < o[s] ? 1u : 0u;
-    if ((lm >> s) & 1) {
-      R |= (uint64_t)r << (4 * s);
-      INV |= (uint64_t)s << (4 * r);
-      if (r == 0) delta = s;
+      for (int t = 0; t < 14; ++t)
+        if (t != s) r += o[t] < o[s] ? 1u : 0u;
+      if ((lm >> s) & 1) {
+        R |= (uint64_t)r << (4 * s);
+        INV |= (uint64_t)s << (4 * r);
+        if (r == 0) delta = s;
+      }
     }
+  } else {
+#ifdef __CUDA_ARCH__
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+      const int s = i + 7 * half;
+      const uint32_t os = half ? o[i + 7] : o[i];
+      uint32_t r = 0;
+#pragma unroll
+      for (int t = 0; t < 14; ++t) r += o[t] < os ? 1u : 0u;
+      if ((lm >> s) & 1) {
+        R |= (uint64_t)r << (4 * s);
+        INV |= (uint64_t)s << (4 * r);
+      }
+    }
+    R |= __shfl_xor_sync(pmask, R, 1);
+    INV |= __shfl_xor_sync(pmask, INV, 1);
+    delta = (int)(INV & 15u);
+#endif
   }
   auto rank = [&](int s) -> uint32_t { return (uint32_t)(R >> (4 * s)) & 15u; };
   auto slot = [&](uint32_t r) -> int { return (int)((INV >> (4 * r)) & 15u); };
@@ -171,9 +199,10 @@ DMS_HD int process_lower_star(uint32_t lm, const uint32_t (&o)[14], const Tables
   const uint32_t QL = lower_tets(tb, lm);
   const uint32_t k = (uint32_t)popc32(lm);
 
-  // the link edges in position space
+  // the link edges in position space (with two lanes, alternate ones each)
   uint32_t E0 = 0, E1 = 0, E2 = 0;
-  for (uint64_t mt = TL; mt; mt &= mt - 1) {
+  const uint64_t TLh = TPV == 1 ? TL : TL & (half ? 0xAAAAAAAAAull : 0x555555555ull);
+  for (uint64_t mt = TLh; mt; mt &= mt - 1) {
     const int j = ffs64(mt);
     const uint32_t p = pos_of(rank(tb.triA[j]), rank(tb.triB[j]));
     const uint32_t b = 1u << (p & 31);
@@ -181,14 +210,25 @@ DMS_HD int process_lower_star(uint32_t lm, const uint32_t (&o)[14], const Tables
     else if (p < 64) E1 |= b;
     else E2 |= b;
   }
+#ifdef __CUDA_ARCH__
+  if constexpr (TPV == 2) {
+    E0 |= __shfl_xor_sync(pmask, E0, 1);
+    E1 |= __shfl_xor_sync(pmask, E1, 1);
+    E2 |= __shfl_xor_sync(pmask, E2, 1);
+  }
+#endif
   // 12-bit keys of the lower-star tets (link triangles)
-  for (uint32_t mq = QL; mq; mq &= mq - 1) {
+  const uint32_t QLh = TPV == 1 ? QL : QL & (half ? 0xAAAAAAu : 0x555555u);
+  for (uint32_t mq = QLh; mq; mq &= mq - 1) {
     const int q = ffs32(mq);
     const uint32_t ra = rank(tb.tetS[q][0]), rb = rank(tb.tetS[q][1]), rc = rank(tb.tetS[q][2]);
     const uint32_t h = umax(ra, umax(rb, rc)), l = umin(ra, umin(rb, rc));
     const uint32_t m = ra + rb + rc - h - l;
     keys.q[q][tid] = (uint16_t)(((h + 1) << 8) | ((m + 1) << 4) | (l + 1));
   }
+#ifdef __CUDA_ARCH__
+  if constexpr (TPV == 2) __syncwarp(pmask);  // both halves of the keys written
+#endif
   auto tet_key = [&](int q) -> uint32_t { return keys.q[q][tid]; };
 
   uint32_t C = 0;                       // classified link vertices (ranks)

@@ -62,7 +62,7 @@ def test_host_side_validation(lib):
 
 def test_batch_host_validation(lib):
     from paper_2505_21266_gb300 import _lib
-    assert lib.dms_batch_tile_variants() == 3
+    assert lib.dms_batch_tile_variants() == 6
     assert lib.dms_batch_max_rounds() > 0
     T = _lib.dms_field_desc * 2
     good = T(_lib.dms_field_desc(0, 4, 5, 6, 0), _lib.dms_field_desc(120, 3, 3, 3, 0))
@@ -81,7 +81,7 @@ def test_batch_host_validation(lib):
         fake, fake, fake, wsb, fake, None)
     assert args(gap, 0, 1 << 40) == 8     # DMS_ERR_ARG: offsets not contiguous
     assert args(thin, 0, 1 << 40) == 2    # DMS_ERR_DIMS
-    assert args(good, 3, 1 << 40) == 8    # no such tile variant
+    assert args(good, 6, 1 << 40) == 8    # no such tile variant
     assert args(good, 0, 16) == 5         # DMS_ERR_WORKSPACE
 
 

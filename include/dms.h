@@ -137,7 +137,14 @@ int dms_order(const float* f, dms_dims d, uint32_t* order, void* ws, size_t ws_b
  *           Triangles paired with an edge are recorded at that edge, those
  *           paired with a tetrahedron at the tetrahedron.
  *   crit_counts [4] int64 out: number of critical simplices per dimension
- *           (overwritten, not accumulated).
+ *           (overwritten, not accumulated).  crit_counts[0] < 0 after the
+ *           call means that a TMA copy of the order field into shared memory
+ *           did not complete within the kernel's wait limit: the outputs are
+ *           then invalid (read it as DMS_ERR_TIMEOUT).
+ * When nx is a multiple of 4 and order is 16-byte aligned, the kernel stages
+ * the order field through TMA (cp.async.bulk.tensor tile loads of one slab
+ * window each, two slabs ahead); otherwise through ordinary loads.  The
+ * results are the same.
  */
 int dms_gradient(const uint32_t* order, dms_dims d, uint8_t* desc, uint64_t* rec,
                  int64_t* crit_counts, void* stream);

@@ -125,6 +125,9 @@ def critical(g: Gradient, caps=None, status: torch.Tensor | None = None):
     d = dims_of(g.desc)
     if caps is None:
         caps = [int(x) for x in g.counts.cpu()]
+        if caps[0] < 0:
+            raise DMSError("dms_gradient: a TMA copy of the order field timed out "
+                           "(DMS_ERR_TIMEOUT); the gradient is invalid")
     lists = [torch.empty(max(int(c), 1), dtype=torch.int64, device=dev) for c in caps]
     cap_arr = (ctypes.c_int64 * 4)(*[int(c) for c in caps])
     counts = torch.empty(4, dtype=torch.int64, device=dev)

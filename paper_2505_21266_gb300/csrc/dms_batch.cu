@@ -21,6 +21,7 @@ size_t order_workspace_bytes_n(int64_t n);
 int launch_order_fields(const float* f, int64_t n, const int64_t* foff, int nfields,
                         uint32_t* order, void* ws, int32_t* dstatus, cudaStream_t s);
 int gradient_tile_height(int variant);
+int gradient_batch_variants();
 int launch_gradient_batch(const uint32_t* order, const dms_field_desc* fields_dev, int nfields,
                           int variant, int zc, uint8_t* desc, uint64_t* rec, int64_t* counts,
                           long long* tile0, unsigned long long* queue, cudaStream_t s);
@@ -39,7 +40,6 @@ int launch_diagram_batch(const float* f, const uint32_t* order, const uint8_t* d
 
 namespace {
 
-constexpr int kTileVariants = 6;  // as dms_gradient.cu
 constexpr int kGradTX = 32;
 
 // vertex offsets of the fields (+ the total) for the segmented sort
@@ -140,7 +140,7 @@ int choose_zc(const dms_field_desc* fh, int nfields, int ty, int sms) {
 
 extern "C" {
 
-int32_t dms_batch_tile_variants(void) { return dms::kTileVariants; }
+int32_t dms_batch_tile_variants(void) { return dms::gradient_batch_variants(); }
 
 int32_t dms_batch_max_rounds(void) { return dms::diagram_batch_rounds(); }
 
@@ -164,7 +164,7 @@ int dms_batch_diagrams(const float* f, const dms_field_desc* fields_host,
   int st = dms::check_fields(fields_host, nfields, &total);
   if (st) return st;
   if (!dms::check_caps(caps, cap_pairs)) return DMS_ERR_ARG;
-  if (tile_variant < 0 || tile_variant >= dms::kTileVariants) return DMS_ERR_ARG;
+  if (tile_variant < 0 || tile_variant >= dms::gradient_batch_variants()) return DMS_ERR_ARG;
   if (!f || !fields_dev || !order || !desc || !rec || !pair_offsets || !d0_essential || !counts ||
       !ws || !dstatus)
     return DMS_ERR_NULL;

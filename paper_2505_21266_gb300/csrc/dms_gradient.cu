@@ -35,7 +35,10 @@
 // time.
 #include <algorithm>
 #include <cstdint>
+#include <cstring>
 #include <type_traits>
+
+#include <cuda.h>  // CUtensorMap (the encoder is fetched from the driver at run time)
 
 #include "dms_common.cuh"
 #include "dms_lowerstar.cuh"
@@ -55,12 +58,22 @@ constexpr uint64_t kEdgeLsb = 0x49249ull;      // bits 0,3,..,18
 constexpr uint64_t kTriMask = 0xFFFull << 21;  // bits 21..32
 constexpr uint64_t kTetLsb = 0x9249ull << 33;  // bits 33,36,..,48
 
-// shared memory of a CTA working on tiles of TX x TY anchors
-template <int TY>
+// shared memory of a CTA working on tiles of TX x TY anchors.  The order
+// field is staged slab by slab in windows of WY rows x WX columns: with TMA
+// (TMA = true) a ring of four windows whose rows start at x0 - 4 (a
+// 16-byte-aligned start: x0 is a multiple of 32) and are TX + 8 wide, else
+// a ring of three windows starting at x0 - 1, TX + 3 wide.  Column XOFF + lx
+// of a window holds grid x = x0 + lx.
+template <int TY, bool TMA = false>
 struct Smem {
-  static constexpr int WX = TX + 3, WY = TY + 3;
+  static constexpr int WY = TY + 3;
+  static constexpr int WX = TMA ? TX + 8 : TX + 3;
+  static constexpr int XOFF = TMA ? 4 : 1;
+  static constexpr int NSLAB = TMA ? 4 : 3;
+  static constexpr int SLAB = (WY * WX + 31) / 32 * 32;  // words; a multiple of 128 bytes
   lowerstar::Tables tb;
-  uint32_t win[3][WY][WX];
+  alignas(128) uint32_t win[NSLAB][SLAB];
+  unsigned long long bar[4];  // TMA: one mbarrier per window
   unsigned long long recs[2][TY][TX];
   lowerstar::Keys<NT> keys;
   uint16_t perm[(TX + 1) * (TY + 1)];  // slab vertices grouped by bucket, largest first
@@ -73,7 +86,7 @@ struct Smem {
 };
 
 template <int TY>
-__device__ __forceinline__ void load_slab(Smem<TY>& sm, const uint32_t* __restrict__ order,
+__device__ __forceinline__ void load_slab(Smem<TY, false>& sm, const uint32_t* __restrict__ order,
                                           const Grid& g, int x0, int y0, int64_t zs, int slot) {
   constexpr int WX = Smem<TY>::WX, WY = Smem<TY>::WY;
   for (int i = threadIdx.x; i < WX * WY; i += NT) {
@@ -82,12 +95,86 @@ __device__ __forceinline__ void load_slab(Smem<TY>& sm, const uint32_t* __restri
     uint32_t v = 0xFFFFFFFFu;
     if (zs >= 0 && zs < g.nz && gx >= 0 && gx < g.nx && gy >= 0 && gy < g.ny)
       v = __ldg(order + gx + g.nx * (gy + g.ny * zs));
-    sm.win[slot][wy][wx] = v;
+    sm.win[slot][i] = v;
   }
 }
 
+// ---- TMA staging (one field; its order array viewed as an nx x ny x nz
+// tensor of u32) ----------------------------------------------------------
+// A window is one box of WX x WY x 1 at (x0 - 4, y0 - 1, zs): loads may start
+// outside the grid (only x has to be 16-byte aligned), and TMA fills what
+// lies outside with zeros, which the border windows then overwrite with
+// 0xFFFFFFFF (never lower).  Each window has an mbarrier; thread 0 arms it
+// with the box's byte count and issues the copy, and every thread waits on
+// its phase, at most kTmaWaitLimit polls (a copy that never lands marks the
+// call failed and the CTA stops, see gradient_kernel).
+constexpr uint32_t kTmaWaitLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
 template <int TY>
-__device__ __forceinline__ void load_tables(Smem<TY>& sm) {
+__device__ __forceinline__ void tma_init(Smem<TY, true>& sm) {
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < 4; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&sm.bar[b])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+}
+
+// thread 0 only; the window's previous contents were last read before a
+// __syncthreads that the caller passed
+template <int TY>
+__device__ __forceinline__ void tma_issue(Smem<TY, true>& sm, const CUtensorMap* tm, int b, int x0,
+                                          int y0, int64_t zs) {
+  constexpr uint32_t kBytes = Smem<TY, true>::WX * Smem<TY, true>::WY * 4;
+  const uint32_t bar = smem_u32(&sm.bar[b]), dst = smem_u32(sm.win[b]);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kBytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(x0 - 4), "r"(y0 - 1), "r"((int)zs), "r"(bar)
+      : "memory");
+}
+
+// waits for the phase `parity` of window b; false after kTmaWaitLimit polls
+template <int TY>
+__device__ __forceinline__ bool tma_wait(Smem<TY, true>& sm, int b, uint32_t parity) {
+  const uint32_t bar = smem_u32(&sm.bar[b]);
+  for (uint32_t it = 0; it < kTmaWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// out-of-grid entries of a window that touches the grid's border -> never lower
+template <int TY>
+__device__ __forceinline__ void tma_fix_border(Smem<TY, true>& sm, const Grid& g, int b, int x0,
+                                               int y0, int64_t zs) {
+  constexpr int WX = Smem<TY, true>::WX, WY = Smem<TY, true>::WY;
+  const bool border = x0 - 4 < 0 || x0 - 4 + WX > g.nx || y0 - 1 < 0 || y0 - 1 + WY > g.ny ||
+                      zs < 0 || zs >= g.nz;
+  if (!border) return;
+  for (int i = threadIdx.x; i < WX * WY; i += NT) {
+    const int64_t gx = x0 - 4 + i % WX, gy = y0 - 1 + i / WX;
+    if (zs < 0 || zs >= g.nz || gx < 0 || gx >= g.nx || gy < 0 || gy >= g.ny)
+      sm.win[b][i] = 0xFFFFFFFFu;
+  }
+}
+
+template <int TY, bool TMA>
+__device__ __forceinline__ void load_tables(Smem<TY, TMA>& sm) {
   static_assert(sizeof(lowerstar::Tables) % 4 == 0, "word copy");
   const uint32_t* src = reinterpret_cast<const uint32_t*>(&cTables);
   uint32_t* dst = reinterpret_cast<uint32_t*>(&sm.tb);
@@ -99,26 +186,73 @@ __device__ __forceinline__ void load_tables(Smem<TY>& sm) {
 // (the +1 halo) slab by slab and writes complete records and desc.  Adds the
 // critical simplices of the written records to ncrit (per thread) and the
 // minima to sm.counts[0].  Requires sm.tb loaded, sm.recs zero.
-template <int TY, int TPV = 1>
-__device__ void gradient_tile(Smem<TY>& sm, const uint32_t* __restrict__ order, const Grid& g,
+// With TMA (tm: the field's tensor map), windows come from the TMA ring,
+// slab z - 1 + i in window i % 4, the slab two ahead in flight while a slab
+// is processed; returns false if a copy did not land (the tile is then
+// left unfinished).
+template <int TY, bool TMA = false, int TPV = 1>
+__device__ bool gradient_tile(Smem<TY, TMA>& sm, const uint32_t* __restrict__ order, const Grid& g,
                               int x0, int y0, int64_t z0, int64_t zend, uint8_t* __restrict__ desc,
-                              uint64_t* __restrict__ rec, unsigned int (&ncrit)[3]) {
+                              uint64_t* __restrict__ rec, unsigned int (&ncrit)[3],
+                              const CUtensorMap* tm = nullptr) {
   constexpr int VPW = 32 / TPV;  // vertices per warp task
-  constexpr int WX = Smem<TY>::WX;
+  constexpr int WX = Smem<TY, TMA>::WX, XOFF = Smem<TY, TMA>::XOFF;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t zlast = (zend < g.nz - 1) ? zend : g.nz - 1;  // vertex slabs [z0, zlast]
-  load_slab(sm, order, g, x0, y0, z0 - 1, (int)((z0 + 2) % 3));
-  load_slab(sm, order, g, x0, y0, z0, (int)(z0 % 3));
+  // TMA: slabs z0 - 1 .. zlast + 1 in order, copy j (slab z0 - 1 + j) in
+  // window j % 4, its wait on phase (j / 4) % 2 of that window's mbarrier
+  int issued = 0, waited = 0;
+  auto issue = [&](int64_t zs) {
+    if constexpr (TMA) {
+      if (tid == 0) tma_issue(sm, tm, issued & 3, x0, y0, zs);
+      ++issued;
+    }
+  };
+  // false (in every thread) if the copy did not land; the copies still in
+  // flight are then waited for, each at most kTmaWaitLimit polls
+  auto wait_next = [&](int64_t zs) -> bool {
+    if constexpr (TMA) {
+      const int b = waited & 3;
+      const bool ok = tma_wait(sm, b, (uint32_t)((waited >> 2) & 1));
+      ++waited;
+      if (!__syncthreads_and(ok)) {
+        for (; waited < issued; ++waited) (void)tma_wait(sm, waited & 3, (uint32_t)((waited >> 2) & 1));
+        return false;
+      }
+      tma_fix_border(sm, g, b, x0, y0, zs);
+    }
+    return true;
+  };
+  if constexpr (TMA) {
+    for (int j = 0; j < 3; ++j) issue(z0 - 1 + j);  // zlast >= z0: all three are needed
+    if (!wait_next(z0 - 1) || !wait_next(z0)) return false;
+  } else {
+    load_slab(sm, order, g, x0, y0, z0 - 1, (int)((z0 + 2) % 3));
+    load_slab(sm, order, g, x0, y0, z0, (int)(z0 % 3));
+  }
 
   const int nvx = TX + 1, nvy = TY + 1;
   const int ntask = (nvx * nvy + VPW - 1) / VPW;
   for (int64_t z = z0; z <= zlast; ++z) {
-    load_slab(sm, order, g, x0, y0, z + 1, (int)((z + 1) % 3));
-    __syncthreads();
     typedef uint32_t Row[WX];
-    const Row* wm = sm.win[(z + 2) % 3];
-    const Row* w0 = sm.win[z % 3];
-    const Row* wp = sm.win[(z + 1) % 3];
+    const Row* wm;
+    const Row* w0;
+    const Row* wp;
+    if constexpr (TMA) {
+      const int i = (int)(z - z0);
+      if (z + 2 <= zlast + 1) issue(z + 2);  // window (i + 3) % 4 was last read before the
+                                             // previous slab's closing __syncthreads
+      if (!wait_next(z + 1)) return false;
+      wm = reinterpret_cast<const Row*>(sm.win[i & 3]);
+      w0 = reinterpret_cast<const Row*>(sm.win[(i + 1) & 3]);
+      wp = reinterpret_cast<const Row*>(sm.win[(i + 2) & 3]);
+    } else {
+      load_slab(sm, order, g, x0, y0, z + 1, (int)((z + 1) % 3));
+      wm = reinterpret_cast<const Row*>(sm.win[(z + 2) % 3]);
+      w0 = reinterpret_cast<const Row*>(sm.win[z % 3]);
+      wp = reinterpret_cast<const Row*>(sm.win[(z + 1) % 3]);
+    }
+    __syncthreads();
     // group the slab's vertices by the trip counts of their lower-star loops
     // so that the lanes of a warp get similar work; warps take groups
     // largest-first
@@ -128,12 +262,12 @@ __device__ void gradient_tile(Smem<TY>& sm, const uint32_t* __restrict__ order, 
       const int lx = i % nvx, ly = i / nvx;
       uint32_t k = 0, lm = 0;
       if (x0 + lx < g.nx && y0 + ly < g.ny) {
-        const uint32_t ox = w0[ly + 1][lx + 1];
+        const uint32_t ox = w0[ly + 1][lx + XOFF];
         static_for<0, 14>([&](auto S) {
           constexpr int s = decltype(S)::value;
           constexpr int dx = kStar.off[s][0], dy = kStar.off[s][1], dz = kStar.off[s][2];
           const Row* w = dz < 0 ? wm : (dz > 0 ? wp : w0);
-          lm |= (w[ly + 1 + dy][lx + 1 + dx] < ox ? 1u : 0u) << s;
+          lm |= (w[ly + 1 + dy][lx + XOFF + dx] < ox ? 1u : 0u) << s;
         });
         const uint32_t kl = __popc(lm), nq = __popc(lowerstar::lower_tets(sm.tb, lm));
         k = kl * 16u + min(nq, 15u);  // < 15 * 16
@@ -172,7 +306,7 @@ __device__ void gradient_tile(Smem<TY>& sm, const uint32_t* __restrict__ order, 
       const int lx = idx % nvx, ly = idx / nvx;
       const int64_t x = x0 + lx, y = y0 + ly;
       if (slot < nvx * nvy && x < g.nx && y < g.ny) {
-        const int cx = lx + 1, cy = ly + 1;
+        const int cx = lx + XOFF, cy = ly + 1;
         uint32_t o[14];
         static_for<0, 14>([&](auto S) {
           constexpr int s = decltype(S)::value;
@@ -227,11 +361,12 @@ __device__ void gradient_tile(Smem<TY>& sm, const uint32_t* __restrict__ order, 
     }
     __syncthreads();
   }
+  return true;
 }
 
 // adds the CTA's critical counts to counts[4] (all threads must call)
-template <int TY>
-__device__ __forceinline__ void add_counts(Smem<TY>& sm, unsigned int (&ncrit)[3],
+template <int TY, bool TMA>
+__device__ __forceinline__ void add_counts(Smem<TY, TMA>& sm, unsigned int (&ncrit)[3],
                                            unsigned long long* counts) {
   const int tid = threadIdx.x, lane = tid & 31;
   for (int d = 0; d < 3; ++d) {
@@ -248,22 +383,30 @@ __device__ __forceinline__ void add_counts(Smem<TY>& sm, unsigned int (&ncrit)[3
   __syncthreads();
 }
 
-// one field, one CTA per tile of anchors
-template <int TY>
+// one field, one CTA per tile of anchors; with TMA the order slabs come
+// through the tensor map tmap.  A TMA copy that does not land sets bit 63
+// of counts[0] (the call has failed) and ends the CTA.
+template <int TY, bool TMA>
 __global__ void __launch_bounds__(NT, 4) gradient_kernel(const uint32_t* __restrict__ order, Grid g,
                                                       int zc, uint8_t* __restrict__ desc,
                                                       uint64_t* __restrict__ rec,
-                                                      unsigned long long* __restrict__ counts) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem<TY>& sm = *reinterpret_cast<Smem<TY>*>(smem_raw);
+                                                      unsigned long long* __restrict__ counts,
+                                                      const __grid_constant__ CUtensorMap tmap) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  Smem<TY, TMA>& sm = *reinterpret_cast<Smem<TY, TMA>*>(smem_raw);
   const int tid = threadIdx.x;
   load_tables(sm);
   for (int i = tid; i < 2 * TX * TY; i += NT) (&sm.recs[0][0][0])[i] = 0ull;
   if (tid < 4) sm.counts[tid] = 0;
+  if constexpr (TMA) tma_init(sm);
   const int64_t z0 = (int64_t)blockIdx.z * zc;
   const int64_t zend = (z0 + zc < g.nz) ? z0 + zc : g.nz;
   unsigned int ncrit[3] = {0, 0, 0};
-  gradient_tile(sm, order, g, blockIdx.x * TX, blockIdx.y * TY, z0, zend, desc, rec, ncrit);
+  if (!gradient_tile<TY, TMA>(sm, order, g, blockIdx.x * TX, blockIdx.y * TY, z0, zend, desc, rec,
+                              ncrit, &tmap)) {
+    if (tid == 0) atomicOr(counts, 1ull << 63);
+    return;
+  }
   add_counts(sm, ncrit, counts);
 }
 
@@ -284,7 +427,7 @@ __global__ void __launch_bounds__(NT, 4) gradient_batch_kernel(const uint32_t* _
                                                             uint8_t* __restrict__ desc,
                                                             uint64_t* __restrict__ rec,
                                                             unsigned long long* __restrict__ counts) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   Smem<TY>& sm = *reinterpret_cast<Smem<TY>*>(smem_raw);
   const int tid = threadIdx.x;
   load_tables(sm);
@@ -316,8 +459,8 @@ __global__ void __launch_bounds__(NT, 4) gradient_batch_kernel(const uint32_t* _
     const long long bx = local % tx, by = (local / tx) % ty, bz = local / ((long long)tx * ty);
     const int64_t z0 = bz * bt.zc;
     const int64_t zend = (z0 + bt.zc < g.nz) ? z0 + bt.zc : g.nz;
-    gradient_tile<TY, TPV>(sm, order + fd.offset, g, (int)bx * TX, (int)by * TY, z0, zend,
-                           desc + fd.offset, rec + fd.offset, ncrit);
+    gradient_tile<TY, false, TPV>(sm, order + fd.offset, g, (int)bx * TX, (int)by * TY, z0, zend,
+                                  desc + fd.offset, rec + fd.offset, ncrit);
     add_counts(sm, ncrit, counts + 4 * lo);
   }
 }
@@ -336,13 +479,50 @@ __global__ void batch_tiles_kernel(const dms_field_desc* __restrict__ fields, in
   *queue = 0ull;
 }
 
+// cuTensorMapEncodeTiled from the driver (the library links only the runtime)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// the order field as an nx x ny x nz u32 tensor with WX x WY x 1 boxes; false
+// where TMA cannot stage it (row pitch not a multiple of 16 bytes, an
+// unaligned pointer, no encoder) -- the kernel then loads with __ldg
 template <int TY>
+bool order_tensor_map(CUtensorMap* m, const uint32_t* order, const Grid& g) {
+  if (g.nx % 4 != 0 || (reinterpret_cast<uintptr_t>(order) & 15) != 0) return false;
+  const EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)g.nx * 4, (cuuint64_t)g.sxy * 4};
+  const cuuint32_t box[3] = {(cuuint32_t)Smem<TY, true>::WX, (cuuint32_t)Smem<TY, true>::WY, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, const_cast<uint32_t*>(order), dims, strides, box,
+            es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int TY, bool TMA>
 int launch_single(const uint32_t* order, const Grid& g, uint8_t* desc, uint64_t* rec,
-                  int64_t* crit_counts, cudaStream_t s) {
+                  int64_t* crit_counts, const CUtensorMap& tmap, cudaStream_t s) {
   static bool configured = false;
-  const size_t smem = sizeof(Smem<TY>);
+  const size_t smem = sizeof(Smem<TY, TMA>);
   if (!configured) {
-    if (cudaFuncSetAttribute(gradient_kernel<TY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(gradient_kernel<TY, TMA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem) != cudaSuccess)
       return DMS_ERR_CUDA;
     configured = true;
@@ -350,7 +530,7 @@ int launch_single(const uint32_t* order, const Grid& g, uint8_t* desc, uint64_t*
   int dev = 0, sms = 148, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gradient_kernel<TY>, NT, smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gradient_kernel<TY, TMA>, NT, smem) !=
           cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
@@ -369,8 +549,8 @@ int launch_single(const uint32_t* order, const Grid& g, uint8_t* desc, uint64_t*
   nzc = (g.nz + zc - 1) / zc;
   if (cudaMemsetAsync(crit_counts, 0, 4 * sizeof(int64_t), s) != cudaSuccess) return DMS_ERR_CUDA;
   dim3 grid((unsigned)tx, (unsigned)ty, (unsigned)nzc);
-  gradient_kernel<TY><<<grid, NT, smem, s>>>(order, g, zc, desc, rec,
-                                             reinterpret_cast<unsigned long long*>(crit_counts)); count_launch();
+  gradient_kernel<TY, TMA><<<grid, NT, smem, s>>>(
+      order, g, zc, desc, rec, reinterpret_cast<unsigned long long*>(crit_counts), tmap); count_launch();
   return launch_status();
 }
 
@@ -407,6 +587,7 @@ int launch_batch(const uint32_t* order, const dms_field_desc* fields_dev, int nf
 // the batch variants the autotuner chooses from: tile height (variant % 3:
 // 24, 16, 32 anchor rows) x lanes per vertex (1 + variant / 3)
 constexpr int kTileVariants = 6;
+int gradient_batch_variants() { return kTileVariants; }
 int gradient_tile_height(int variant) {
   const int t = variant % 3;
   return t == 1 ? 16 : (t == 2 ? 32 : 24);
@@ -414,7 +595,11 @@ int gradient_tile_height(int variant) {
 
 int launch_gradient(const uint32_t* order, const Grid& g, uint8_t* desc, uint64_t* rec,
                     int64_t* crit_counts, cudaStream_t s) {
-  return launch_single<24>(order, g, desc, rec, crit_counts, s);
+  CUtensorMap tmap;
+  if (order_tensor_map<24>(&tmap, order, g))
+    return launch_single<24, true>(order, g, desc, rec, crit_counts, tmap, s);
+  std::memset(&tmap, 0, sizeof(tmap));
+  return launch_single<24, false>(order, g, desc, rec, crit_counts, tmap, s);
 }
 
 int launch_gradient_batch(const uint32_t* order, const dms_field_desc* fields_dev, int nfields,

@@ -125,9 +125,8 @@ def critical(g: Gradient, caps=None, status: torch.Tensor | None = None):
     d = dims_of(g.desc)
     if caps is None:
         caps = [int(x) for x in g.counts.cpu()]
-        if caps[0] < 0:
-            raise DMSError("dms_gradient: a TMA copy of the order field timed out "
-                           "(DMS_ERR_TIMEOUT); the gradient is invalid")
+        if caps[0] < 0:  # a TMA copy of the order field did not land: invalid gradient
+            raise DMSError(7, "dms_gradient")  # DMS_ERR_TIMEOUT
     lists = [torch.empty(max(int(c), 1), dtype=torch.int64, device=dev) for c in caps]
     cap_arr = (ctypes.c_int64 * 4)(*[int(c) for c in caps])
     counts = torch.empty(4, dtype=torch.int64, device=dev)
@@ -277,8 +276,9 @@ def diagrams_from_host(fields_host, device="cuda"):
     def enqueue(i, x):
         if not isinstance(x, torch.Tensor):
             x = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32))
-        if bufs[i] is None or bufs[i].shape != x.shape:
-            bufs[i] = torch.empty(x.shape, dtype=torch.float32, device=dev)
+        for j in (i, 1 - i):  # both buffers at the first field (and at a new shape)
+            if bufs[j] is None or bufs[j].shape != x.shape:
+                bufs[j] = torch.empty(x.shape, dtype=torch.float32, device=dev)
         copier.wait_stream(compute)  # the buffer's last reader is done
         with torch.cuda.stream(copier):
             bufs[i].copy_(x, non_blocking=True)

@@ -565,7 +565,7 @@ def main():
         h2d = host.numel() * 4
         # the other legs' buffers go back to the device first; the warm-up
         # runs the same two-buffer stream, so the timed region allocates nothing
-        del d, st, c
+        d = st = c = None
         torch.cuda.empty_cache()
         for _ in dms.diagrams_from_host([host] * max(2, args.warmup), dev):
             pass

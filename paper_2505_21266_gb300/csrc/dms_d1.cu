@@ -211,10 +211,17 @@ __device__ __forceinline__ void ent_edge(const Grid& g, const HEnt& e, int64_t& 
 }
 
 // ---- heap in the pool -------------------------------------------------------
+// An 8-ary max-heap (children of i: 8i+1 .. 8i+8): a pop reads a node's
+// children together (independent loads, adjacent in memory), so the chain of
+// dependent accesses of a pop is log8 of the size, a third of a binary
+// heap's; the boundaries of the last columns reach 1e4-1e5 edges, and each
+// is worked by one thread.
+constexpr uint32_t kHeapArity = 8;
+
 __device__ __forceinline__ void heap_push(HEnt* h, uint32_t& size, const HEnt& e) {
   uint32_t i = size++;
   while (i > 0) {
-    const uint32_t p = (i - 1) >> 1;
+    const uint32_t p = (i - 1) / kHeapArity;
     if (h[p].key >= e.key) break;
     h[i] = h[p];
     i = p;
@@ -226,12 +233,22 @@ __device__ __forceinline__ HEnt heap_pop(HEnt* h, uint32_t& size) {
   const HEnt last = h[--size];
   uint32_t i = 0;
   for (;;) {
-    uint32_t l = 2 * i + 1;
-    if (l >= size) break;
-    if (l + 1 < size && h[l + 1].key > h[l].key) ++l;
-    if (h[l].key <= last.key) break;
-    h[i] = h[l];
-    i = l;
+    const uint32_t c0 = kHeapArity * i + 1;
+    if (c0 >= size) break;
+    unsigned long long k[kHeapArity];
+#pragma unroll
+    for (uint32_t j = 0; j < kHeapArity; ++j) k[j] = c0 + j < size ? h[c0 + j].key : 0ull;
+    uint32_t b = 0;
+    unsigned long long bk = k[0];
+#pragma unroll
+    for (uint32_t j = 1; j < kHeapArity; ++j)
+      if (k[j] > bk) {
+        bk = k[j];
+        b = j;
+      }
+    if (bk <= last.key) break;
+    h[i] = h[c0 + b];
+    i = c0 + b;
   }
   if (size) h[i] = last;
   return top;

@@ -14,7 +14,17 @@
 //     ballots on its bits, then popc), stages it in shared memory in digit
 //     order and writes it out;
 //   * the first active pass reads the float field itself (payload = index),
-//     the last one scatters order[payload] = position instead of writing keys.
+//     the last one scatters order[payload] = position instead of writing keys;
+//   * on a large single field that scatter -- 4-byte writes to random
+//     vertices, each a sector read and write in DRAM -- is replaced by an
+//     inverse permutation in three streaming passes: the last pass writes
+//     the sorted payloads in position order like any other pass; then
+//     (vertex, position) pairs are grouped by slices of 2^23 vertices, then
+//     by slices of 2^14 (tile-local counting sorts in shared memory, so the
+//     global writes are runs); each 2^14-vertex slice is finally scattered
+//     in shared memory and written out whole.  The order is a permutation,
+//     so every slice of vertex ids holds exactly its size in pairs and
+//     needs no histogram: one atomic cursor per slice places the runs.
 #include <algorithm>
 #include <cstdint>
 
@@ -33,6 +43,20 @@ constexpr int SCAN_CHUNK = SCAN_NT * SCAN_ITEMS;
 
 enum : int { SRC_FIELD = 0, SRC_A = 1, SRC_B = 2, DST_A = 1, DST_B = 2, DST_ORDER = 3 };
 
+// the inverse-permutation passes (single fields from kInvMin vertices on;
+// below that order[] sits in L2 and the direct scatter is cheap)
+constexpr int INV_NT = 256;
+constexpr int INV_ITEMS = 16;
+constexpr int INV_TILE = INV_NT * INV_ITEMS;  // 4096
+constexpr int FINE_SHIFT = 14;                // 2^14 vertices: 64 KiB of order[] in shared memory
+constexpr int COARSE_SHIFT = 23;              // 2^23 vertices
+constexpr int COARSE_BINS = 512;              // n < 2^32
+constexpr int FINE_BINS = 1 << (COARSE_SHIFT - FINE_SHIFT);  // 512 per coarse slice
+constexpr int CUR_STRIDE = 8;                 // one cursor per 32-byte sector
+constexpr int64_t kInvMin = (int64_t)1 << 25;
+static_assert(INV_TILE <= (1 << COARSE_SHIFT) && ((1 << COARSE_SHIFT) % INV_TILE) == 0,
+              "a tile of the fine pass lies in one coarse slice");
+
 // passes 0-3: the four bytes of the key; passes 4-5: the two bytes of the
 // field index of a vertex when several fields are sorted at once (their
 // vertices are concatenated; each field gets its own order)
@@ -43,6 +67,7 @@ struct Plan {
   int src[kPasses];
   int dst[kPasses];
   int any;
+  int last_src;  // source of the last active pass (its other buffers are then free)
 };
 
 struct Fields {
@@ -104,11 +129,13 @@ __global__ void plan_kernel(const unsigned int* __restrict__ ghist, int64_t n, i
       ++cnt;
     }
   int cur = SRC_FIELD, k = 0;
+  plan->last_src = SRC_FIELD;
   for (int p = 0; p < kPasses; ++p) {
     plan->active[p] = act[p];
     plan->src[p] = plan->dst[p] = 0;
     if (!act[p]) continue;
     plan->src[p] = cur;
+    plan->last_src = cur;
     int dst = (p == last) ? DST_ORDER : ((k & 1) ? DST_B : DST_A);
     plan->dst[p] = dst;
     cur = dst;
@@ -286,7 +313,7 @@ struct DownSmem {
 __global__ void __launch_bounds__(SORT_NT, 4) downsweep_kernel(
     int pass, const Plan* __restrict__ plan, const float* __restrict__ f, uint32_t* ka,
     uint32_t* kb, uint32_t* va, uint32_t* vb, uint32_t* __restrict__ order, const Fields fl,
-    int64_t n, int64_t ntiles, const unsigned int* __restrict__ th) {
+    int64_t n, int64_t ntiles, const unsigned int* __restrict__ th, bool inverse) {
   if (!plan->active[pass]) return;
   const int src = plan->src[pass], dst = plan->dst[pass];
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -361,7 +388,11 @@ __global__ void __launch_bounds__(SORT_NT, 4) downsweep_kernel(
     const uint32_t v = sm.sv[p];
     uint32_t d = digit_of(pass, k, v, fl);
     uint32_t g = sm.goff[d] + (p - sm.dstart[d]);
-    if (dst == DST_ORDER) {
+    if (dst == DST_ORDER && inverse) {
+      // the payloads in position order, in the value buffer this pass does
+      // not read; the inverse-permutation passes build order[] from them
+      (src == SRC_A ? vb : va)[g] = v;
+    } else if (dst == DST_ORDER) {
       // position within the vertex's own field
       order[v] = fl.n > 1 ? g - (uint32_t)__ldg(fl.off + field_of(fl, v)) : g;
     } else {
@@ -369,6 +400,121 @@ __global__ void __launch_bounds__(SORT_NT, 4) downsweep_kernel(
       vd[g] = sm.sv[p];
     }
   }
+}
+
+// One bucketing pass of the inverse permutation.  Input: pairs (v, p) --
+// v from inV, p from inP, or p = the element's index when inP is null (the
+// sorted payloads); the last pass's output buffer is picked from the plan
+// when inV is null.  Each pair goes to region R = v >> shift of the output,
+// [R << shift, (R + 1) << shift), at a place from R's cursor; a tile groups
+// its pairs by bin = R % nbins in shared memory first (R of one tile differ
+// in their bin: the coarse pass has R < nbins, a tile of the fine pass lies
+// in one coarse slice), so that the global writes are runs.  Order within a
+// region is free: the last pass scatters each region by v.
+struct InvSmem {
+  unsigned int cnt[COARSE_BINS];   // per bin: count, then start in the tile
+  unsigned int base[COARSE_BINS];  // per bin: place of the tile's run in its region
+  uint32_t sv[INV_TILE], sp[INV_TILE];
+  unsigned int tmp[32];
+};
+
+__global__ void __launch_bounds__(INV_NT) inv_bucket_kernel(
+    const Plan* __restrict__ plan, uint32_t* va, uint32_t* vb, const uint32_t* inV,
+    const uint32_t* __restrict__ inP, int64_t n, int shift, int nbins, uint32_t* __restrict__ outV,
+    uint32_t* __restrict__ outP, unsigned int* __restrict__ cur) {
+  if (!plan->any) return;
+  __shared__ InvSmem sm;
+  if (!inV) inV = plan->last_src == SRC_A ? vb : va;
+  const int64_t t0 = (int64_t)blockIdx.x * INV_TILE;
+  const int cntT = (int)((n - t0 < INV_TILE) ? n - t0 : INV_TILE);
+  for (int b = threadIdx.x; b < nbins; b += INV_NT) sm.cnt[b] = 0;
+  __syncthreads();
+  uint32_t v[INV_ITEMS], pp[INV_ITEMS];
+  unsigned short loc[INV_ITEMS];
+#pragma unroll
+  for (int r = 0; r < INV_ITEMS; ++r) {
+    const int i = threadIdx.x + r * INV_NT;
+    if (i < cntT) {
+      v[r] = __ldcs(inV + t0 + i);
+      pp[r] = inP ? __ldcs(inP + t0 + i) : (uint32_t)(t0 + i);
+      loc[r] = (unsigned short)atomicAdd(&sm.cnt[(v[r] >> shift) & (nbins - 1)], 1u);
+    }
+  }
+  __syncthreads();
+  // bins -> starts in the tile (exclusive scan, two bins per thread) and
+  // the runs' places in their regions
+  {
+    const int b0 = 2 * threadIdx.x;
+    const unsigned int c0 = b0 < nbins ? sm.cnt[b0] : 0u, c1 = b0 + 1 < nbins ? sm.cnt[b0 + 1] : 0u;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned int x = c0 + c1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) sm.tmp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      unsigned int w = lane < INV_NT / 32 ? sm.tmp[lane] : 0u;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int y = __shfl_up_sync(0xFFFFFFFFu, w, o);
+        if (lane >= o) w += y;
+      }
+      sm.tmp[lane] = w;
+    }
+    __syncthreads();
+    const unsigned int start = x - (c0 + c1) + (warp > 0 ? sm.tmp[warp - 1] : 0u);
+    if (b0 < nbins) sm.cnt[b0] = start;
+    if (b0 + 1 < nbins) sm.cnt[b0 + 1] = start + c0;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < INV_ITEMS; ++r) {
+    const int i = threadIdx.x + r * INV_NT;
+    if (i < cntT) {
+      const unsigned int at = sm.cnt[(v[r] >> shift) & (nbins - 1)] + loc[r];
+      sm.sv[at] = v[r];
+      sm.sp[at] = pp[r];
+    }
+  }
+  __syncthreads();
+  // one cursor atomic per bin present in the tile; its region from the
+  // bin's first pair (all pairs of a bin share the region)
+  for (int b = threadIdx.x; b < nbins; b += INV_NT) {
+    const unsigned int st = sm.cnt[b];
+    const unsigned int en = (b + 1 < nbins) ? sm.cnt[b + 1] : (unsigned int)cntT;
+    sm.base[b] = en > st ? atomicAdd(cur + (size_t)((sm.sv[st] >> shift)) * CUR_STRIDE, en - st) : 0u;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < cntT; i += INV_NT) {
+    const uint32_t vv = sm.sv[i];
+    const uint32_t R = vv >> shift;
+    const int b = (int)(R & (uint32_t)(nbins - 1));
+    const int64_t at = ((int64_t)R << shift) + sm.base[b] + (i - (int)sm.cnt[b]);
+    if (at < n) {  // always, for a permutation
+      outV[at] = vv;
+      outP[at] = sm.sp[i];
+    }
+  }
+}
+
+// The last pass of the inverse permutation: one CTA per 2^14-vertex slice
+// scatters its pairs into the slice of order[] held in shared memory and
+// writes it out whole.
+__global__ void __launch_bounds__(512) inv_scatter_kernel(const Plan* __restrict__ plan,
+                                                          const uint32_t* __restrict__ Zv,
+                                                          const uint32_t* __restrict__ Zp,
+                                                          int64_t n, uint32_t* __restrict__ order) {
+  if (!plan->any) return;
+  extern __shared__ uint32_t slice[];  // [1 << FINE_SHIFT]
+  const int64_t s0 = (int64_t)blockIdx.x << FINE_SHIFT;
+  const int len = (int)((n - s0 < (1 << FINE_SHIFT)) ? n - s0 : (1 << FINE_SHIFT));
+  for (int i = threadIdx.x; i < len; i += blockDim.x)
+    slice[__ldcs(Zv + s0 + i) & ((1u << FINE_SHIFT) - 1)] = __ldcs(Zp + s0 + i);
+  __syncthreads();
+  for (int i = threadIdx.x; i < len; i += blockDim.x) order[s0 + i] = slice[i];
 }
 
 __global__ void identity_kernel(const Plan* __restrict__ plan, uint32_t* order, int64_t n) {
@@ -383,6 +529,8 @@ struct OrderWs {
   unsigned int* th;
   unsigned int* sums;
   unsigned int* ghist;
+  unsigned int* cur;  // inverse permutation: coarse then fine slice cursors
+  int64_t ncur;
   Plan* plan;
   size_t bytes;
 };
@@ -399,6 +547,8 @@ OrderWs carve_order(void* base, int64_t n) {
   w.th = c.take<unsigned int>(m);
   w.sums = c.take<unsigned int>((m + SCAN_CHUNK - 1) / SCAN_CHUNK + 1);
   w.ghist = c.take<unsigned int>(1024);
+  w.ncur = ((int64_t)COARSE_BINS + (n >> FINE_SHIFT) + 1) * CUR_STRIDE;
+  w.cur = c.take<unsigned int>(w.ncur);
   w.plan = c.take<Plan>(1);
   w.bytes = c.used;
   return w;
@@ -427,10 +577,13 @@ int launch_order_fields(const float* f, int64_t n, const int64_t* foff, int nfie
   static bool configured = false;
   if (!configured) {
     if (cudaFuncSetAttribute(downsweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(DownSmem)) != cudaSuccess)
+                             (int)sizeof(DownSmem)) != cudaSuccess ||
+        cudaFuncSetAttribute(inv_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(uint32_t) << FINE_SHIFT)) != cudaSuccess)
       return DMS_ERR_CUDA;
     configured = true;
   }
+  const bool inverse = nfields == 1 && n >= kInvMin;
   DMS_CUDA_OK(cudaMemsetAsync(w.ghist, 0, 1024 * sizeof(unsigned int), s));
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
@@ -446,7 +599,21 @@ int launch_order_fields(const float* f, int64_t n, const int64_t* foff, int nfie
     scan_sums_kernel<<<1, SCAN_NT, 0, s>>>(p, w.plan, w.sums, nsums); count_launch();
     scan_down_kernel<<<(unsigned)nsums, SCAN_NT, 0, s>>>(p, w.plan, w.th, m, w.sums); count_launch();
     downsweep_kernel<<<(unsigned)ntiles, SORT_NT, sizeof(DownSmem), s>>>(
-        p, w.plan, f, w.ka, w.kb, w.va, w.vb, order, fl, n, ntiles, w.th); count_launch();
+        p, w.plan, f, w.ka, w.kb, w.va, w.vb, order, fl, n, ntiles, w.th, inverse); count_launch();
+  }
+  if (inverse) {
+    // sorted payloads -> (vertex, position) by coarse slice (ka, kb) -> by
+    // fine slice (va, vb) -> order[], slice by slice in shared memory
+    DMS_CUDA_OK(cudaMemsetAsync(w.cur, 0, (size_t)w.ncur * sizeof(unsigned int), s));
+    const unsigned itiles = (unsigned)((n + INV_TILE - 1) / INV_TILE);
+    inv_bucket_kernel<<<itiles, INV_NT, 0, s>>>(w.plan, w.va, w.vb, nullptr, nullptr, n,
+                                                COARSE_SHIFT, COARSE_BINS, w.ka, w.kb, w.cur); count_launch();
+    inv_bucket_kernel<<<itiles, INV_NT, 0, s>>>(w.plan, w.va, w.vb, w.ka, w.kb, n, FINE_SHIFT,
+                                                FINE_BINS, w.va, w.vb,
+                                                w.cur + (size_t)COARSE_BINS * CUR_STRIDE); count_launch();
+    const unsigned slices = (unsigned)((n + (1 << FINE_SHIFT) - 1) >> FINE_SHIFT);
+    inv_scatter_kernel<<<slices, 512, sizeof(uint32_t) << FINE_SHIFT, s>>>(w.plan, w.va, w.vb, n,
+                                                                           order); count_launch();
   }
   int64_t ib = std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
   identity_kernel<<<(unsigned)ib, 256, 0, s>>>(w.plan, order, n); count_launch();

@@ -1,4 +1,5 @@
-"""The gradient kernel's two ways of staging the order field: TMA tile loads
+"""Large-field paths: the gradient kernel's two ways of staging the order
+field, and the order stage's inverse permutation.  Staging: TMA tile loads
 (row pitch a multiple of 16 bytes, order 16-byte aligned) and plain loads
 (otherwise).  Both must give the same records, and the TMA path must match
 the oracle on grids whose x tiles, y tiles and z chunks all end ragged, so
@@ -63,3 +64,20 @@ def test_tma_path_matches_oracle(shape):
         assert np.array_equal(pairs, r.get(oracle.GRAD_PAIRS))
         for d in range(4):
             assert np.array_equal(crit[d], r.crit(d))
+
+
+@pytest.mark.parametrize("kind", ["quantised", "mixture"])
+def test_order_inverse_permutation_path(kind):
+    """Fields of at least 2^25 vertices build order[] from the sorted
+    payloads by the bucketed inverse permutation; it must equal the inverse
+    of a stable argsort, here on a size whose last slices are partial."""
+    shape = (330, 320, 320)  # 33,792,000 vertices
+    if kind == "quantised":
+        f = fields.quantized_noise(shape, 64, 5).cuda()
+    else:
+        f = fields.gaussian_mixture(shape, 16, (0.05, 0.2), 1e-2, 5, device="cuda")
+    o = dms.order(f).reshape(-1).to(torch.int64)
+    idx = torch.sort(f.reshape(-1) + 0.0, stable=True).indices
+    inv = torch.empty_like(idx)
+    inv[idx] = torch.arange(idx.numel(), device=idx.device)
+    assert torch.equal(o, inv)

@@ -572,13 +572,16 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         d2h = 0
+        marks = []
         for d0, d2, ess in dms.diagrams_from_host([host] * args.steps, dev):
             d2h = d0.nbytes + d2.nbytes + ess.nbytes
+            marks.append(time.perf_counter())
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         e2e = {"value": nvert * world * args.steps / dt, "unit": "vertices/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "overlap": "next field's host-to-device copy on a second stream"}
+               "overlap": "next field's host-to-device copy on a second stream",
+               "field_ms": [round(1e3 * (b - a), 1) for a, b in zip([t0] + marks, marks)]}
 
     hbm_peak, sm_mhz, peak_kind = load_peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count

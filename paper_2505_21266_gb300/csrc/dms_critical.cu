@@ -27,6 +27,13 @@ __device__ __forceinline__ void anchor_counts(uint8_t d, uint64_t r, int c[4]) {
   c[3] = __popcll(r & (r >> 1) & (r >> 2) & kTetLsb);
 }
 
+// a thread's four counts as 16-bit fields (bits 16d..16d+15 for dimension d)
+__device__ __forceinline__ long long pack_counts(const int (&tot)[4]) {
+  static_assert(CTILE * 12 < 65536, "a tile's count of any dimension fits 16 bits");
+  return (long long)tot[0] | ((long long)tot[1] << 16) | ((long long)tot[2] << 32) |
+         ((long long)tot[3] << 48);
+}
+
 // A thread works on CITEMS consecutive anchors, so consecutive threads read
 // shared memory CITEMS elements apart; one pad element per CITEMS spreads
 // those reads over the banks.
@@ -84,11 +91,12 @@ __global__ void __launch_bounds__(CNT) count_kernel(const uint8_t* __restrict__ 
     if (a0 + i >= n) c[0] = 0;
     for (int d = 0; d < 4; ++d) tot[d] += c[d];
   }
-  for (int d = 0; d < 4; ++d) {
-    long long t;
-    scan64::block_excl(tot[d], sm.tmp, &t);
-    if (threadIdx.x == 0) bc[d * ntiles + blockIdx.x] = t;
-  }
+  // the four counts in 16-bit fields of one word (a tile's totals stay
+  // below 2^16 in every field), so one block scan serves all four lists
+  long long t;
+  scan64::block_excl(pack_counts(tot), sm.tmp, &t);
+  if (threadIdx.x == 0)
+    for (int d = 0; d < 4; ++d) bc[d * ntiles + blockIdx.x] = (t >> (16 * d)) & 0xFFFF;
 }
 
 // the critical ids of one anchor a (record r, desc d), in type order, to
@@ -141,10 +149,12 @@ __global__ void __launch_bounds__(CNT) write_kernel(const uint8_t* __restrict__ 
     for (int d = 0; d < 4; ++d) tot[d] += c[d];
   }
   long long loc[4];
-  for (int d = 0; d < 4; ++d) {
+  {
     long long t;
-    loc[d] = scan64::block_excl(tot[d], sm.tmp, &t);
-    if (threadIdx.x == 0) tcount[d] = t;
+    const long long e = scan64::block_excl(pack_counts(tot), sm.tmp, &t);
+    for (int d = 0; d < 4; ++d) loc[d] = (e >> (16 * d)) & 0xFFFF;
+    if (threadIdx.x == 0)
+      for (int d = 0; d < 4; ++d) tcount[d] = (t >> (16 * d)) & 0xFFFF;
   }
   if (threadIdx.x == 0) {
     long long acc = 0;

@@ -276,9 +276,10 @@ def diagrams_from_host(fields_host, device="cuda"):
     def enqueue(i, x):
         if not isinstance(x, torch.Tensor):
             x = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32))
-        for j in (i, 1 - i):  # both buffers at the first field (and at a new shape)
-            if bufs[j] is None or bufs[j].shape != x.shape:
-                bufs[j] = torch.empty(x.shape, dtype=torch.float32, device=dev)
+        if bufs[i] is None or bufs[i].shape != x.shape:
+            bufs[i] = torch.empty(x.shape, dtype=torch.float32, device=dev)
+        if bufs[1 - i] is None:  # the other buffer too, at the first field
+            bufs[1 - i] = torch.empty(x.shape, dtype=torch.float32, device=dev)
         copier.wait_stream(compute)  # the buffer's last reader is done
         with torch.cuda.stream(copier):
             bufs[i].copy_(x, non_blocking=True)

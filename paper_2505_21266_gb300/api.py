@@ -267,10 +267,13 @@ def diagrams_from_host(fields_host, device="cuda"):
     essential class as numpy structured arrays, like diagram_from_host.
     The host-to-device copy of the next field runs on a separate stream
     while the current field goes through the path, into the second of two
-    device buffers, so the copies hide behind the compute."""
+    device buffers; a field's pairs come back to page-locked host memory on
+    a third stream while the next field goes through the path, so a field's
+    arrays are yielded after the next field's path is under way."""
     dev = torch.device(device)
     compute = torch.cuda.current_stream(dev)
     copier = torch.cuda.Stream(dev)
+    drain = torch.cuda.Stream(dev)
     bufs, ready = [None, None], [None, None]
 
     def enqueue(i, x):
@@ -286,23 +289,47 @@ def diagrams_from_host(fields_host, device="cuda"):
             ready[i] = torch.cuda.Event()
             ready[i].record(copier)
 
+    def start_drain(res):
+        """The field's pair lists to page-locked host memory on `drain`."""
+        drain.wait_stream(compute)
+        outs = []
+        with torch.cuda.stream(drain):
+            for t in (res.diagrams.d0, res.diagrams.d2, res.diagrams.d0_essential):
+                h = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+                h.copy_(t, non_blocking=True)
+                t.record_stream(drain)  # the device list outlives the copy
+                outs.append(h)
+            done = torch.cuda.Event()
+            done.record(drain)
+        return outs, done
+
+    def finish(p):
+        outs, done = p
+        done.synchronize()
+        return tuple(h.numpy().view(PAIR_DTYPE).reshape(-1) for h in outs)
+
     it = iter(fields_host)
     nxt = next(it, None)
     if nxt is None:
         return
     cur = 0
     enqueue(cur, nxt)
+    pending = None
     while True:
         compute.wait_event(ready[cur])
         nxt = next(it, None)
         if nxt is not None:
             enqueue(1 - cur, nxt)  # overlaps the path below
         res = diagram(bufs[cur])
-        yield (res.diagrams.numpy("d0"), res.diagrams.numpy("d2"),
-               res.diagrams.numpy("d0_essential"))
+        p = start_drain(res)
+        del res
+        if pending is not None:
+            yield finish(pending)  # the previous field; its copy ran behind this path
+        pending = p
         if nxt is None:
-            return
+            break
         cur = 1 - cur
+    yield finish(pending)
 
 
 # ------------------------------------------------------------------ diff --

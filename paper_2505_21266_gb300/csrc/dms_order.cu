@@ -15,7 +15,7 @@
 //     order and writes it out;
 //   * the first active pass reads the float field itself (payload = index),
 //     the last one scatters order[payload] = position instead of writing keys;
-//   * on a large single field that scatter -- 4-byte writes to random
+//   * on a large field (or batch of fields) that scatter -- 4-byte writes to random
 //     vertices, each a sector read and write in DRAM -- is replaced by an
 //     inverse permutation in three streaming passes: the last pass writes
 //     the sorted payloads in position order like any other pass; then
@@ -43,7 +43,7 @@ constexpr int SCAN_CHUNK = SCAN_NT * SCAN_ITEMS;
 
 enum : int { SRC_FIELD = 0, SRC_A = 1, SRC_B = 2, DST_A = 1, DST_B = 2, DST_ORDER = 3 };
 
-// the inverse-permutation passes (single fields from kInvMin vertices on;
+// the inverse-permutation passes (a field, or a batch of fields, of at least kInvMin vertices;
 // below that order[] sits in L2 and the direct scatter is cheap)
 constexpr int INV_NT = 512;   // 3 CTAs per SM at 40 registers (the
 constexpr int INV_ITEMS = 8;  // bucketing is latency-bound: warps in flight count)
@@ -503,10 +503,13 @@ __global__ void __launch_bounds__(INV_NT, 3) inv_bucket_kernel(
 // The last pass of the inverse permutation: one CTA per 2^14-vertex slice
 // scatters its pairs into the slice of order[] held in shared memory and
 // writes it out whole.
+// With several fields (concatenated, each with its own order) a position
+// is made local to the vertex's field on the way out.
 __global__ void __launch_bounds__(512) inv_scatter_kernel(const Plan* __restrict__ plan,
                                                           const uint32_t* __restrict__ Zv,
                                                           const uint32_t* __restrict__ Zp,
-                                                          int64_t n, uint32_t* __restrict__ order) {
+                                                          const Fields fl, int64_t n,
+                                                          uint32_t* __restrict__ order) {
   if (!plan->any) return;
   extern __shared__ uint32_t slice[];  // [1 << FINE_SHIFT]
   const int64_t s0 = (int64_t)blockIdx.x << FINE_SHIFT;
@@ -514,7 +517,10 @@ __global__ void __launch_bounds__(512) inv_scatter_kernel(const Plan* __restrict
   for (int i = threadIdx.x; i < len; i += blockDim.x)
     slice[__ldcs(Zv + s0 + i) & ((1u << FINE_SHIFT) - 1)] = __ldcs(Zp + s0 + i);
   __syncthreads();
-  for (int i = threadIdx.x; i < len; i += blockDim.x) order[s0 + i] = slice[i];
+  for (int i = threadIdx.x; i < len; i += blockDim.x) {
+    const uint32_t v = (uint32_t)(s0 + i);
+    order[s0 + i] = fl.n > 1 ? slice[i] - (uint32_t)__ldg(fl.off + field_of(fl, v)) : slice[i];
+  }
 }
 
 __global__ void identity_kernel(const Plan* __restrict__ plan, uint32_t* order, int64_t n) {
@@ -583,7 +589,7 @@ int launch_order_fields(const float* f, int64_t n, const int64_t* foff, int nfie
       return DMS_ERR_CUDA;
     configured = true;
   }
-  const bool inverse = nfields == 1 && n >= kInvMin;
+  const bool inverse = n >= kInvMin;
   DMS_CUDA_OK(cudaMemsetAsync(w.ghist, 0, 1024 * sizeof(unsigned int), s));
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
@@ -612,8 +618,8 @@ int launch_order_fields(const float* f, int64_t n, const int64_t* foff, int nfie
                                                 FINE_BINS, w.va, w.vb,
                                                 w.cur + (size_t)COARSE_BINS * CUR_STRIDE); count_launch();
     const unsigned slices = (unsigned)((n + (1 << FINE_SHIFT) - 1) >> FINE_SHIFT);
-    inv_scatter_kernel<<<slices, 512, sizeof(uint32_t) << FINE_SHIFT, s>>>(w.plan, w.va, w.vb, n,
-                                                                           order); count_launch();
+    inv_scatter_kernel<<<slices, 512, sizeof(uint32_t) << FINE_SHIFT, s>>>(w.plan, w.va, w.vb, fl,
+                                                                           n, order); count_launch();
   }
   int64_t ib = std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8);
   identity_kernel<<<(unsigned)ib, 256, 0, s>>>(w.plan, order, n); count_launch();

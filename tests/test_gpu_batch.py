@@ -18,6 +18,7 @@ pytestmark = pytest.mark.gpu
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
+import paper_2505_21266_gb300 as dms
 from paper_2505_21266_gb300 import batch as B
 from paper_2505_21266_gb300 import fields
 
@@ -128,6 +129,31 @@ def test_batch_equals_per_field_path():
         _same(a0, c0)
         _same(a2, c2)
         assert ae["birth_id"][0] == ce["birth_id"][0]
+
+
+def test_large_batch_order_and_pairs_equal_per_field():
+    """A batch of at least 2^25 vertices builds its per-field orders by the
+    bucketed inverse permutation (positions made local to each field on the
+    way out); each field alone (under 2^25 vertices) uses the direct
+    scatter.  Orders and pairs must agree field by field."""
+    shapes = [(200, 230, 256), (190, 247, 251), (200, 250, 250)]  # 36,055,430 vertices
+    assert sum(a * b * c for a, b, c in shapes) >= 1 << 25
+    xs = [fields.batch_field(i, s, seed=9, device="cuda") for i, s in enumerate(shapes)]
+    b = B.Batch(shapes, "cuda")
+    b.set_fields(xs)
+    b.fit()
+    torch.cuda.synchronize()
+    for i, x in enumerate(xs):
+        mine = b.order[b.offsets[i]:b.offsets[i + 1]].view(torch.int32).reshape(x.shape)
+        assert torch.equal(mine, dms.order(x).view(torch.int32))
+    got = b.results()
+    ref = B.per_field(xs)
+    for (a0, a2, ae), (c0, c2, ce) in zip(got, ref):
+        _same(a0, c0)
+        _same(a2, c2)
+        assert ae["birth_id"][0] == ce["birth_id"][0]
+    del b, xs
+    torch.cuda.empty_cache()
 
 
 def test_capacity_growth():

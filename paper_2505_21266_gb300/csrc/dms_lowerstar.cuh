@@ -84,6 +84,8 @@ struct Tables {
   uint8_t tetS[24][3];  // slots of tet q
   uint8_t tetF[24][3];
   uint8_t tetCode[24][3];  // record code (1..4) when tet q pairs with facet tetF[q][w]
+  uint8_t tetCodeOf[24][36];  // the same by the facet's star triangle (0: not a facet)
+  uint16_t c3[16];            // binomial C(h, 3)
   uint8_t triOfSlots[14][14];  // star triangle on slots (a, b), 255 if none
   // position of the star triangle on slots (a, b) among the cofacets of the
   // edge of slot a (the record's edge code minus one)
@@ -224,7 +226,10 @@ DMS_HD int process_lower_star(uint32_t lm, const uint32_t (&o)[14], const Tables
     const uint32_t ra = rank(tb.tetS[q][0]), rb = rank(tb.tetS[q][1]), rc = rank(tb.tetS[q][2]);
     const uint32_t h = umax(ra, umax(rb, rc)), l = umin(ra, umin(rb, rc));
     const uint32_t m = ra + rb + rc - h - l;
-    keys.q[q][tid] = (uint16_t)(((h + 1) << 8) | ((m + 1) << 4) | (l + 1));
+    // the rank triple h > m > l by its combinatorial index (increasing with
+    // the key), the tet in the low five bits: a candidate's minimum is then
+    // the smallest key and names its tet
+    keys.q[q][tid] = (uint16_t)(((tb.c3[h] + ((m * (m - 1)) >> 1) + l) << 5) | (uint32_t)q);
   }
 #ifdef __CUDA_ARCH__
   if constexpr (TPV == 2) __syncwarp(pmask);  // both halves of the keys written
@@ -283,17 +288,12 @@ DMS_HD int process_lower_star(uint32_t lm, const uint32_t (&o)[14], const Tables
     for (;;) {
       while (pQ) {
         uint32_t bestQ = 0xFFFFu;
-        int q = 0;
-        for (uint32_t m = pQ; m; m &= m - 1) {
-          const int qq = ffs32(m);
-          const uint32_t kq = tet_key(qq);
-          if (kq < bestQ) { bestQ = kq; q = qq; }
-        }
+        for (uint32_t m = pQ; m; m &= m - 1) bestQ = umin(bestQ, tet_key(ffs32(m)));
+        const int q = (int)(bestQ & 31u);
         pQ &= ~(1u << q);
         if ((Q3 >> q) & 1) continue;  // no unclassified edge left: PQzero
         const int beta = ffs64(~cT & tb.tetFmask[q]);
-        const int w = beta == tb.tetF[q][0] ? 0 : (beta == tb.tetF[q][1] ? 1 : 2);
-        set_tet_code(q, tb.tetCode[q][w]);
+        set_tet_code(q, tb.tetCodeOf[q][beta]);
         cQ |= 1u << q;
         classify_edge(beta);
         pQ |= tb.triCof[beta] & QL & Q2 & ~Q3 & ~cQ;
@@ -311,14 +311,17 @@ DMS_HD int process_lower_star(uint32_t lm, const uint32_t (&o)[14], const Tables
         const uint32_t ke = ((umax(ra, rb) + 1) << 8) | ((umin(ra, rb) + 1) << 4);
         if (ke < bestE) { bestE = ke; je = jj; }
       }
-      uint32_t bestQ = 0xFFFFu;
+      uint32_t bestQ = 0xFFFFu, bestQkey = 0xFFFFu;
       int q = 0;
-      for (uint32_t m = zQ; m; m &= m - 1) {
-        const int qq = ffs32(m);
-        const uint32_t kq = tet_key(qq);
-        if (kq < bestQ) { bestQ = kq; q = qq; }
+      if (zQ) {
+        for (uint32_t m = zQ; m; m &= m - 1) bestQ = umin(bestQ, tet_key(ffs32(m)));
+        q = (int)(bestQ & 31u);
+        // the winner's key in the edges' nibble form, for the comparison
+        const uint32_t ra = rank(tb.tetS[q][0]), rb = rank(tb.tetS[q][1]), rc = rank(tb.tetS[q][2]);
+        const uint32_t h = umax(ra, umax(rb, rc)), l = umin(ra, umin(rb, rc));
+        bestQkey = ((h + 1) << 8) | ((ra + rb + rc - h - l + 1) << 4) | (l + 1);
       }
-      if (bestE < bestQ) {  // a critical link edge: a critical triangle of L
+      if (bestE < bestQkey) {  // a critical link edge: a critical triangle of L
         const int j = je;
         critT |= 1ull << j;
         classify_edge(j);
@@ -369,6 +372,7 @@ constexpr Tables make_tables() {
     for (int w = 0; w < 3; ++w) {
       t.tetF[i][w] = (uint8_t)kStar.tetF[i][w];
       t.tetCode[i][w] = (uint8_t)kStar.facetCode[i][w];
+      t.tetCodeOf[i][kStar.tetF[i][w]] = (uint8_t)kStar.facetCode[i][w];
     }
     t.tetS[i][0] = (uint8_t)kStar.tetA[i];
     t.tetS[i][1] = (uint8_t)kStar.tetB[i];
@@ -389,6 +393,7 @@ constexpr Tables make_tables() {
   }
   for (int h = 1; h < 14; ++h)
     for (int l = 0; l < h; ++l) t.hlOfPos[h * (h - 1) / 2 + l] = (uint8_t)((h << 4) | l);
+  for (int h = 0; h < 16; ++h) t.c3[h] = (uint16_t)(h * (h - 1) * (h - 2) / 6);
   for (int i = 0; i < 64; ++i) t.bit[i] = 1ull << i;
   for (int i = 0; i < 16; ++i) t.nib[i] = 1ull << (4 * i);
   for (int r = 0; r < 14; ++r) {

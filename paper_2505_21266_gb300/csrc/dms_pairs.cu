@@ -269,6 +269,7 @@ __global__ void d0_weights(Dev D, const uint32_t* __restrict__ order,
   uint32_t r = local_rank(D, order, top, oa > ob ? ob : oa);
   T.s[i].w = ((uint64_t)(oa > ob ? oa : ob) << 4) | r;
   T.s[i].res = kNone;
+  T.s[i].ra = T.s[i].rb = kNone;  // walk results pending
 }
 
 // The two cofacets of critical triangle id (anchor a, type k) in field g
@@ -322,6 +323,7 @@ __global__ void d2_weights(Dev D, const uint32_t* __restrict__ order,
   uint64_t key = ((uint64_t)o[it] << 8) | (rm << 4) | rl;
   T.s[i].w = kMask44 - key;
   T.s[i].res = kNone;
+  T.s[i].ra = T.s[i].rb = kNone;  // walk results pending
 }
 
 // ---------------------------------------------------------------------------
@@ -553,6 +555,14 @@ __global__ void __launch_bounds__(256) walk_queue(const W wk, const int64_t* n_d
     if (cur != kNone) {
       uint32_t r = 0;
       if (!wk.step(st, cur, r, dstatus)) {
+        // joined another walk: take its result if it is already known (its
+        // end node, or a link one hop further), so that link_walks has
+        // fewer links to follow; a pending one (kNone) keeps the link
+        if (r & kLinkBit) {
+          const uint32_t w2 = r & ~kLinkBit;
+          const uint32_t r2 = (w2 & 1) ? T.s[w2 >> 1].rb : T.s[w2 >> 1].ra;
+          if (r2 != kNone) r = r2;
+        }
         store_walk(T, cur, r);
         cur = kNone;
       }
@@ -1389,6 +1399,7 @@ __global__ void b_d0_weights(const FieldTab ft, const uint32_t* __restrict__ ord
     const uint32_t r = local_rank_f(g, fd.offset, order, top, oa > ob ? ob : oa);
     T.s[i].w = ((uint64_t)(oa > ob ? oa : ob) << 4) | r;
     T.s[i].res = kNone;
+    T.s[i].ra = T.s[i].rb = kNone;  // walk results pending
   }
 }
 
@@ -1457,6 +1468,7 @@ __global__ void b_d2_weights(const FieldTab ft, const uint32_t* __restrict__ ord
     const uint64_t key = ((uint64_t)o[it] << 8) | (rm << 4) | rl;
     T.s[i].w = kMask44 - key;
     T.s[i].res = kNone;
+    T.s[i].ra = T.s[i].rb = kNone;  // walk results pending
   }
 }
 
@@ -1862,6 +1874,7 @@ __global__ void d0_weights2d(Grid2d g, const uint32_t* __restrict__ order,
   const int64_t top = oa > ob ? a : b;
   T.s[i].w = ((uint64_t)(oa > ob ? oa : ob) << 4) | local_rank2d(g, order, top, oa > ob ? ob : oa);
   T.s[i].res = kNone;
+  T.s[i].ra = T.s[i].rb = kNone;  // walk results pending
   T.s[i].pad = 0;
 }
 
@@ -1883,6 +1896,7 @@ __global__ void d1_weights2d(Grid2d g, const uint32_t* __restrict__ order,
   // a D0 death or a D1 birth: the edges D0 paired take no part in D1.
   T.s[i].pad = T.s[i].res != kNone ? 1u : 0u;
   T.s[i].res = kNone;
+  T.s[i].ra = T.s[i].rb = kNone;  // walk results pending
 }
 
 // node 0 = OUTSIDE (age 0, the oldest); node j + 1 = maximum crit2[j], a

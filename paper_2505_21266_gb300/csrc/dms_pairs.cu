@@ -433,21 +433,25 @@ struct DualWalk {
   const int64_t* crit2;
   const uint64_t* rec;
   uint32_t* claim;
+  // the walk's tet (anchor b, type k), the anchor's coordinates and the
+  // grid's strides and bounds in 32-bit form where they fit
   struct State {
-    Grid g;
-    int64_t b, bx, by, bz, it;
-    int k;
+    int64_t b, sy, sz;
+    int bx, by, bz, k;
+    uint32_t mx, my, mz;  // dims - 1: a tet anchor lies below them in every axis
+    uint32_t it, lim;
   };
   __device__ __forceinline__ bool start(int64_t s, int j, State& st, uint32_t& r) const {
     const int64_t id = crit2[s];
     const int64_t a = id / 12;
     const int k = (int)(id - a * 12);
+    Grid g;
     int64_t off;
-    fields.get(a, st.g, off);
+    fields.get(a, g, off);
     int64_t ax, ay, az;
-    fields.coords(st.g, a - off, ax, ay, az);
+    fields.coords(g, a - off, ax, ay, az);
     int64_t cof[2];
-    tri_cofacets(st.g, a, k, ax, ay, az, cof);
+    tri_cofacets(g, a, k, ax, ay, az, cof);
     const int64_t t = j ? cof[1] : cof[0];
     if (t < 0) {
       r = 0;  // no cofacet on that side: the walk starts OUTSIDE
@@ -455,8 +459,18 @@ struct DualWalk {
     }
     st.b = t / 6;
     st.k = (int)(t - st.b * 6);
-    fields.coords(st.g, st.b - off, st.bx, st.by, st.bz);
+    int64_t bx, by, bz;
+    fields.coords(g, st.b - off, bx, by, bz);
+    st.bx = (int)bx;
+    st.by = (int)by;
+    st.bz = (int)bz;
+    st.sy = g.nx;
+    st.sz = g.sxy;
+    st.mx = (uint32_t)(g.nx - 1);
+    st.my = (uint32_t)(g.ny - 1);
+    st.mz = (uint32_t)(g.nz - 1);
     st.it = 0;
+    st.lim = (uint32_t)min(6 * g.n, (int64_t)0xFFFFFFFF);
     return true;
   }
   // record load and claim in flight together, as for the descending walks;
@@ -483,13 +497,15 @@ struct DualWalk {
     st.bx += sg * (stp & 1);
     st.by += sg * ((stp >> 1) & 1);
     st.bz += sg * ((stp >> 2) & 1);
-    if (!fits(st.g, st.bx, st.by, st.bz, 7)) {
+    // the anchor of a tet needs +1 inside in every axis (negative -> huge)
+    if ((uint32_t)st.bx >= st.mx || (uint32_t)st.by >= st.my || (uint32_t)st.bz >= st.mz) {
       r = 0;  // left the grid: OUTSIDE
       return false;
     }
-    st.b += sg * corner_delta(st.g, stp);
+    const int64_t d = (int64_t)(stp & 1) + (((stp >> 1) & 1) ? st.sy : 0) + (((stp >> 2) & 1) ? st.sz : 0);
+    st.b += sg * d;
     st.k = (int)(t & 7u);
-    if (++st.it > 6 * st.g.n) {
+    if (++st.it > st.lim) {
       set_status(dstatus, DMS_ERR_TIMEOUT);
       r = 0;
       return false;

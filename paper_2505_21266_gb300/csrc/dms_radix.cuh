@@ -23,6 +23,7 @@ __global__ void __launch_bounds__(NT) upsweep(const unsigned long long* __restri
                                               int shift, int64_t ntiles, long long* __restrict__ th,
                                               const unsigned int* n_dev = nullptr) {
   if (n_dev && (int64_t)*n_dev < n) n = *n_dev;
+  if (n == 0) return;  // nothing to sort (a device count of zero)
   __shared__ unsigned int h[WARPS][256];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < WARPS * 256; i += NT) (&h[0][0])[i] = 0;
@@ -59,6 +60,7 @@ __global__ void __launch_bounds__(NT) downsweep(const unsigned long long* __rest
                                                 int64_t ntiles, const long long* __restrict__ th,
                                                 const unsigned int* n_dev = nullptr) {
   if (n_dev && (int64_t)*n_dev < n) n = *n_dev;
+  if (n == 0) return;  // nothing to sort (a device count of zero)
   extern __shared__ __align__(16) unsigned char smem_raw[];
   DownSmem& sm = *reinterpret_cast<DownSmem*>(smem_raw);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -173,7 +175,7 @@ inline bool sort(Buffers& b, int64_t n, int bits, cudaStream_t s,
     unsigned long long* ko = in_a ? b.kb : b.ka;
     uint32_t* vo = in_a ? b.vb : b.va;
     upsweep<<<(unsigned)ntiles, NT, 0, s>>>(ki, n, shift, ntiles, b.th, n_dev); count_launch();
-    scan64::run(b.th, m, b.sums, s);
+    scan64::run(b.th, m, b.sums, s, n_dev);
     downsweep<<<(unsigned)ntiles, NT, sizeof(DownSmem), s>>>(ki, vi, ko, vo, n, shift, ntiles, b.th,
                                                             n_dev); count_launch();
     in_a = !in_a;

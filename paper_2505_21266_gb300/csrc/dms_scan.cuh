@@ -40,8 +40,13 @@ __device__ __forceinline__ long long block_excl(long long v, long long* tmp, lon
   return excl;
 }
 
+// skip (optional): a device count; when it is zero the kernels do nothing
+// (a scan whose consumer has no work, in launch sequences that never
+// synchronise the host)
 __global__ void __launch_bounds__(NT) reduce_kernel(const long long* __restrict__ a, int64_t m,
-                                                    long long* sums) {
+                                                    long long* sums,
+                                                    const unsigned int* skip = nullptr) {
+  if (skip && *skip == 0) return;
   __shared__ long long tmp[32];
   const int64_t base = (int64_t)blockIdx.x * CHUNK;
   long long s = 0;
@@ -55,7 +60,9 @@ __global__ void __launch_bounds__(NT) reduce_kernel(const long long* __restrict_
 }
 
 // scans sums[0..nsums) in place; writes the grand total to sums[nsums]
-__global__ void __launch_bounds__(NT) sums_kernel(long long* sums, int64_t nsums) {
+__global__ void __launch_bounds__(NT) sums_kernel(long long* sums, int64_t nsums,
+                                                  const unsigned int* skip = nullptr) {
+  if (skip && *skip == 0) return;
   __shared__ long long tmp[32];
   __shared__ long long carry;
   if (threadIdx.x == 0) carry = 0;
@@ -74,7 +81,9 @@ __global__ void __launch_bounds__(NT) sums_kernel(long long* sums, int64_t nsums
 }
 
 __global__ void __launch_bounds__(NT) down_kernel(long long* __restrict__ a, int64_t m,
-                                                  const long long* __restrict__ sums) {
+                                                  const long long* __restrict__ sums,
+                                                  const unsigned int* skip = nullptr) {
+  if (skip && *skip == 0) return;
   __shared__ long long tmp[32];
   const int64_t base = (int64_t)blockIdx.x * CHUNK + (int64_t)threadIdx.x * ITEMS;
   long long v[ITEMS];
@@ -98,15 +107,16 @@ inline int64_t num_sums(int64_t m) { return (m + CHUNK - 1) / CHUNK; }
 
 // in-place exclusive scan of a[0..m); sums needs num_sums(m) + 1 entries and
 // receives the total at sums[num_sums(m)]
-inline void run(long long* a, int64_t m, long long* sums, cudaStream_t s) {
+inline void run(long long* a, int64_t m, long long* sums, cudaStream_t s,
+                const unsigned int* skip = nullptr) {
   int64_t ns = num_sums(m);
   if (ns == 0) {
     cudaMemsetAsync(sums, 0, sizeof(long long), s);
     return;
   }
-  reduce_kernel<<<(unsigned)ns, NT, 0, s>>>(a, m, sums); count_launch();
-  sums_kernel<<<1, NT, 0, s>>>(sums, ns); count_launch();
-  down_kernel<<<(unsigned)ns, NT, 0, s>>>(a, m, sums); count_launch();
+  reduce_kernel<<<(unsigned)ns, NT, 0, s>>>(a, m, sums, skip); count_launch();
+  sums_kernel<<<1, NT, 0, s>>>(sums, ns, skip); count_launch();
+  down_kernel<<<(unsigned)ns, NT, 0, s>>>(a, m, sums, skip); count_launch();
 }
 
 }  // namespace scan64

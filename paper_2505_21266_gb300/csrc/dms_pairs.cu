@@ -1505,9 +1505,11 @@ __global__ void b_forest_done(const unsigned int* __restrict__ live_n, int32_t* 
   if (threadIdx.x == 0 && blockIdx.x == 0 && *live_n != 0) set_status(dstatus, DMS_ERR_TIMEOUT);
 }
 
+// As link_walks with tag set: also the forest's first round search (both
+// ends recorded as roots and tagged), so the rounds start at their hook.
 __global__ void __launch_bounds__(256) b_link_walks(const int64_t* __restrict__ n_dev, Tri T,
                                                     uint32_t* live, unsigned int* live_n,
-                                                    int32_t* dstatus) {
+                                                    int32_t* dstatus, Nodes nd) {
   __shared__ CtaAppend sh;
   const int64_t nt = *n_dev;
   // CTA-uniform passes: every thread reaches the appends
@@ -1521,6 +1523,11 @@ __global__ void __launch_bounds__(256) b_link_walks(const int64_t* __restrict__ 
       if (n0 != n1) {
         T.s[i].na = n0;
         T.s[i].nb = n1;
+        T.s[i].ra = n0;
+        T.s[i].rb = n1;
+        const unsigned long long tv = (1ull << 44) | (kMask44 - T.s[i].w);
+        if (n0 != nd.immortal) atomicMax(nd.best + n0, tv);
+        if (n1 != nd.immortal) atomicMax(nd.best + n1, tv);
         keep = true;
       }
     }
@@ -1746,7 +1753,9 @@ int launch_diagram_batch(const float* f, const uint32_t* order, const uint8_t* d
     mem_ok = mem_ok && cudaMemsetAsync(forest_n, 0, sizeof(unsigned int), s) == cudaSuccess;
     for (int r = 1; r <= kBoruvkaRounds; ++r) {
       mem_ok = mem_ok && cudaMemsetAsync(nxt_n, 0, sizeof(unsigned int), s) == cudaSuccess;
-      round_find<<<G, TB, 0, s>>>(cur, cur_n, T, w.nd, (uint64_t)r); count_launch();
+      if (r > 1) {  // b_link_walks did round 1's search
+        round_find<<<G, TB, 0, s>>>(cur, cur_n, T, w.nd, (uint64_t)r); count_launch();
+      }
       boruvka_hook<<<G, TB, 0, s>>>(cur, cur_n, T, w.nd, (uint64_t)r, nxt, nxt_n, w.forest,
                                     forest_n); count_launch();
       std::swap(cur, nxt);
@@ -1796,8 +1805,8 @@ int launch_diagram_batch(const float* f, const uint32_t* order, const uint8_t* d
     const DescWalk<ManyFields> wk{ManyFields{fields_dev, nfields}, crit[1], desc, w.claim};
     DMS_TRY(launch_walks(wk, cnt_dev + 1, 0, w.ctr + 6, w.T0, dstatus, s));
   }
-  b_link_walks<<<G, TB, 0, s>>>(cnt_dev + 1, w.T0, w.live0, w.ctr + 0, dstatus); count_launch();
   w.nd.immortal = kNone;
+  b_link_walks<<<G, TB, 0, s>>>(cnt_dev + 1, w.T0, w.live0, w.ctr + 0, dstatus, w.nd); count_launch();
   rounds(w.T0, cnt_dev + 0, 0);
   write(0, w.T0, crit[0], crit[1], cnt_dev + 1, d0, pair_offsets, pair_totals + 0, fcount);
 
@@ -1811,8 +1820,8 @@ int launch_diagram_batch(const float* f, const uint32_t* order, const uint8_t* d
     const DualWalk<ManyFields> wk{ManyFields{fields_dev, nfields}, crit[2], rec, w.claim};
     DMS_TRY(launch_walks(wk, cnt_dev + 2, 0, w.ctr + 6, w.T2, dstatus, s));
   }
-  b_link_walks<<<G, TB, 0, s>>>(cnt_dev + 2, w.T2, w.live0, w.ctr + 0, dstatus); count_launch();
   w.nd.immortal = 0;  // OUTSIDE, shared by all fields
+  b_link_walks<<<G, TB, 0, s>>>(cnt_dev + 2, w.T2, w.live0, w.ctr + 0, dstatus, w.nd); count_launch();
   rounds(w.T2, cnt_dev + 3, 1);
   write(2, w.T2, crit[2], crit[3], cnt_dev + 2, d2, pair_offsets + (nfields + 1), pair_totals + 1,
         fcount + (nfields + 1));

@@ -33,8 +33,8 @@
 namespace dms {
 namespace {
 
-constexpr int SORT_NT = 512;  // 3 CTAs per SM at 40 registers: the passes wait on
-                               // loads and ranking, so warps in flight count
+constexpr int SORT_NT = 512;  // 4 CTAs per SM at 32 registers (a few spilled): the
+                               // passes wait on loads and ranking, so warps in flight count
 constexpr int SORT_ITEMS = 8;
 constexpr int SORT_TILE = SORT_NT * SORT_ITEMS;  // 4096
 constexpr int SORT_WARPS = SORT_NT / 32;
@@ -311,7 +311,7 @@ struct DownSmem {
   uint32_t sv[SORT_TILE];
 };
 
-__global__ void __launch_bounds__(SORT_NT, 3) downsweep_kernel(
+__global__ void __launch_bounds__(SORT_NT, 4) downsweep_kernel(
     int pass, const Plan* __restrict__ plan, const float* __restrict__ f, uint32_t* ka,
     uint32_t* kb, uint32_t* va, uint32_t* vb, uint32_t* __restrict__ order, const Fields fl,
     int64_t n, int64_t ntiles, const unsigned int* __restrict__ th, bool inverse) {

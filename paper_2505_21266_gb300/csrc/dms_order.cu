@@ -46,7 +46,7 @@ enum : int { SRC_FIELD = 0, SRC_A = 1, SRC_B = 2, DST_A = 1, DST_B = 2, DST_ORDE
 
 // the inverse-permutation passes (a field, or a batch of fields, of at least kInvMin vertices;
 // below that order[] sits in L2 and the direct scatter is cheap)
-constexpr int INV_NT = 512;   // 3 CTAs per SM at 40 registers (the
+constexpr int INV_NT = 512;   // 4 CTAs per SM at 32 registers (the
 constexpr int INV_ITEMS = 8;  // bucketing is latency-bound: warps in flight count)
 constexpr int INV_TILE = INV_NT * INV_ITEMS;  // 4096
 constexpr int FINE_SHIFT = 14;                // 2^14 vertices: 64 KiB of order[] in shared memory
@@ -419,7 +419,7 @@ struct InvSmem {
   unsigned int tmp[32];
 };
 
-__global__ void __launch_bounds__(INV_NT, 3) inv_bucket_kernel(
+__global__ void __launch_bounds__(INV_NT, 4) inv_bucket_kernel(
     const Plan* __restrict__ plan, uint32_t* va, uint32_t* vb, const uint32_t* inV,
     const uint32_t* __restrict__ inP, int64_t n, int shift, int nbins, uint32_t* __restrict__ outV,
     uint32_t* __restrict__ outP, unsigned int* __restrict__ cur) {

@@ -66,16 +66,23 @@ def test_tma_path_matches_oracle(shape):
             assert np.array_equal(crit[d], r.crit(d))
 
 
-@pytest.mark.parametrize("kind", ["quantised", "mixture"])
+@pytest.mark.parametrize("kind", ["quantised", "mixture", "one_byte", "constant"])
 def test_order_inverse_permutation_path(kind):
     """Fields of at least 2^25 vertices build order[] from the sorted
     payloads by the bucketed inverse permutation; it must equal the inverse
-    of a stable argsort, here on a size whose last slices are partial."""
+    of a stable argsort, here on a size whose last slices are partial.
+    "one_byte": only one key byte varies (one sort pass, reading the field
+    itself); "constant": no pass at all (ties: the identity)."""
     shape = (330, 320, 320)  # 33,792,000 vertices
     if kind == "quantised":
         f = fields.quantized_noise(shape, 64, 5).cuda()
-    else:
+    elif kind == "mixture":
         f = fields.gaussian_mixture(shape, 16, (0.05, 0.2), 1e-2, 5, device="cuda")
+    elif kind == "one_byte":  # 1 + j/128: only the top mantissa byte varies
+        j = fields.quantized_noise(shape, 128, 6).cuda() * 128.0
+        f = 1.0 + j / 128.0
+    else:
+        f = torch.full(shape, 0.5, dtype=torch.float32, device="cuda")
     o = dms.order(f).reshape(-1).to(torch.int64)
     idx = torch.sort(f.reshape(-1) + 0.0, stable=True).indices
     inv = torch.empty_like(idx)

@@ -467,7 +467,19 @@ __global__ void __launch_bounds__(256) advance(Grid g, const uint32_t* __restric
       }
       HEnt* h = w.pool + c.off;
       const HEnt* src = w.pool + oo.off;
-      for (uint32_t i = 0; i < oo.size; ++i) heap_push(h, c.size, src[i]);
+      // the other boundary read eight entries at a time (independent loads
+      // in flight together, one line), then pushed: in the last rounds a
+      // column adds thousands of entries per merge, and each push is
+      // otherwise a chain of two dependent loads
+      uint32_t i = 0;
+      for (; i + 8 <= oo.size; i += 8) {
+        HEnt buf[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) buf[j] = src[i + j];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) heap_push(h, c.size, buf[j]);
+      }
+      for (; i < oo.size; ++i) heap_push(h, c.size, src[i]);
       c.pivot = kNone;
     }
     w.col[j] = c;

@@ -272,9 +272,12 @@ int dms_diagram_d0d2_selfcorrecting(const float* f, const uint32_t* order, const
  *   d1   [cap1] out: D1 pairs (birth = edge, death = triangle) in increasing
  *        triangle-id order (n_crit[2] - n_d2 of them); n_out [1] int64 out
  *        (capacity errors as in dms_critical).
- *   pool_entries  16-byte heap entries of the boundary pool (0: 96 per
- *        critical triangle + 65536; at least 16 per critical triangle); a boundary that outgrows the pool sets
- *        (1 << DMS_ERR_CAPACITY) and the call can be repeated with more.
+ *   pool_entries  16-byte heap entries of the boundary pool (0: 256 per
+ *        critical triangle + 65536; at least 16 per critical triangle).  The
+ *        pool is a bump allocator: a heap that grows moves to a new segment
+ *        twice its size and its old one is not reused.  A boundary that
+ *        outgrows the pool sets (1 << DMS_ERR_CAPACITY) and the call can be
+ *        repeated with more (from the start: the rounds before are lost).
  *   ws   at least dms_diagram_d1_workspace_size(d, n_crit, pool_entries).
  * Synchronises `stream` once per round; past 4096 rounds it returns
  * DMS_ERR_TIMEOUT.

@@ -187,8 +187,8 @@ def diagram_d0d2(field: torch.Tensor, order_t: torch.Tensor, g: Gradient, crit,
 
 
 # boundary-pool entries per critical triangle that the last D1 call needed
-# (the library's default is 96); later calls start from it
-_d1_pool_ratio = [96]
+# (the library's default is 256); later calls start from it
+_d1_pool_ratio = [256]
 
 
 def diagram_d1(field: torch.Tensor, order_t: torch.Tensor, g: Gradient, crit, dg: Diagrams,
@@ -210,6 +210,12 @@ def diagram_d1(field: torch.Tensor, order_t: torch.Tensor, g: Gradient, crit, dg
     n_out = torch.zeros(1, dtype=torch.int64, device=dev)
     ratio = _d1_pool_ratio[0]
     pool = int(pool_entries) if pool_entries else ratio * max(nc[2], 1) + 65536
+    if not pool_entries:
+        # a repeated call starts from scratch, so the first one gets as much
+        # of the free memory as the ratio asks for (16-byte entries, a fifth
+        # of the free memory left for the rest of the workspace)
+        free = torch.cuda.mem_get_info(dev)[0]
+        pool = max(min(pool, int(free * 0.8) // 16), 16 * max(nc[2], 1) + 65536)
     for _ in range(max_tries):
         ws = _ws(lib.dms_diagram_d1_workspace_size(d, ncarr, pool), dev)
         st = torch.zeros(1, dtype=torch.int32, device=dev)

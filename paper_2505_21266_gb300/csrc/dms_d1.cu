@@ -589,7 +589,10 @@ constexpr int64_t kExpandLimit = 1ll << 26;  // heap pops of one column in one r
 
 }  // namespace
 
-int64_t d1_default_pool(int64_t n2) { return n2 * (int64_t)kCap0 * 6 + 65536; }
+// a run on quantised noise takes 108-128 entries per critical triangle by its
+// end (abandoned segments included, 192^3 and 256^3); twice that, so that
+// one attempt finishes
+int64_t d1_default_pool(int64_t n2) { return n2 * (int64_t)kCap0 * 16 + 65536; }
 
 size_t d1_workspace_bytes(int64_t n1, int64_t n2, int64_t pool_entries) {
   if (pool_entries <= 0) pool_entries = d1_default_pool(n2);

@@ -585,8 +585,8 @@ def main():
         e2e = {"value": nvert * world * args.steps / dt, "unit": "vertices/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "overlap": "next field's host-to-device copy on a second stream; pairs copied "
-                          "back on a third stream behind the next field's path (a field's "
-                          "arrays arrive one field later)",
+                          "back on a third stream while the next field's gradient kernel runs "
+                          "(a field's arrays arrive one field later)",
                "field_ms": [round(1e3 * (b - a), 1) for a, b in zip([t0] + marks, marks)]}
 
     hbm_peak, sm_mhz, peak_kind = load_peaks()

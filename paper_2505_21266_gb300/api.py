@@ -273,9 +273,12 @@ def diagrams_from_host(fields_host, device="cuda"):
     essential class as numpy structured arrays, like diagram_from_host.
     The host-to-device copy of the next field runs on a separate stream
     while the current field goes through the path, into the second of two
-    device buffers; a field's pairs come back to page-locked host memory on
-    a third stream while the next field goes through the path, so a field's
-    arrays are yielded after the next field's path is under way."""
+    device buffers.  A field's pairs come back to page-locked host memory on
+    a third stream once the next field's order and gradient kernels are
+    queued: the path's small reads of counts go through the same
+    device-to-host copy engine, and behind a copy of the pair lists they
+    would wait for all of it, while the gradient kernel reads nothing on the
+    host.  So a field's arrays are yielded after the next field's path."""
     dev = torch.device(device)
     compute = torch.cuda.current_stream(dev)
     copier = torch.cuda.Stream(dev)
@@ -295,12 +298,13 @@ def diagrams_from_host(fields_host, device="cuda"):
             ready[i] = torch.cuda.Event()
             ready[i].record(copier)
 
-    def start_drain(res):
-        """The field's pair lists to page-locked host memory on `drain`."""
-        drain.wait_stream(compute)
+    def start_drain(dg, end):
+        """A field's pair lists to page-locked host memory on `drain`, after
+        the event `end` that closes the field's path."""
+        drain.wait_event(end)
         outs = []
         with torch.cuda.stream(drain):
-            for t in (res.diagrams.d0, res.diagrams.d2, res.diagrams.d0_essential):
+            for t in (dg.d0, dg.d2, dg.d0_essential):
                 h = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
                 h.copy_(t, non_blocking=True)
                 t.record_stream(drain)  # the device list outlives the copy
@@ -320,22 +324,30 @@ def diagrams_from_host(fields_host, device="cuda"):
         return
     cur = 0
     enqueue(cur, nxt)
-    pending = None
+    prev = None  # the last field's pair lists and the event after its path
     while True:
         compute.wait_event(ready[cur])
         nxt = next(it, None)
         if nxt is not None:
             enqueue(1 - cur, nxt)  # overlaps the path below
-        res = diagram(bufs[cur])
-        p = start_drain(res)
-        del res
-        if pending is not None:
-            yield finish(pending)  # the previous field; its copy ran behind this path
-        pending = p
+        f = bufs[cur]
+        st = torch.zeros(1, dtype=torch.int32, device=dev)
+        o = order(f, status=st)
+        g = gradient(o)
+        p = start_drain(*prev) if prev is not None else None
+        prev = None
+        _device_status_check(st, "dms_order")
+        dg = diagram_d0d2(f, o, g, critical(g))
+        end = torch.cuda.Event()
+        end.record(compute)
+        prev = (dg, end)
+        del o, g, dg
+        if p is not None:
+            yield finish(p)  # the previous field; its copy ran behind this gradient
         if nxt is None:
             break
         cur = 1 - cur
-    yield finish(pending)
+    yield finish(start_drain(*prev))
 
 
 # ------------------------------------------------------------------ diff --

@@ -175,3 +175,20 @@ def test_stream_of_host_fields_matches_one_by_one():
             b = b[np.argsort(b[key], kind="stable")]
             assert mine.tobytes() == b.tobytes()
         assert ess["birth_id"][0] == r.get(oracle.D0_ESSENTIAL)["birth_id"][0]
+
+
+def test_stream_reports_a_nan_field():
+    """In a stream of host fields the order's NaN check is read after the
+    gradient kernel is queued (the sort flags a NaN and still writes a
+    permutation); a NaN in the second field still raises the order's error,
+    before the first field's arrays, which come after the second's path."""
+    good = fields.gaussian_mixture((12, 13, 14), 4, (0.1, 0.3), 1e-3, 0).numpy()
+    bad = good.copy()
+    bad[5, 6, 7] = np.nan
+    out = []
+    with pytest.raises(dms.DMSError) as e:
+        for res in dms.diagrams_from_host([torch.from_numpy(good).pin_memory(),
+                                           torch.from_numpy(bad).pin_memory()]):
+            out.append(res)
+    assert e.value.code == 3
+    assert len(out) == 0  # the first field's arrays come after the second's path

@@ -4,9 +4,10 @@
 // (the stratification of Sec. 2.5) by homologous propagation.
 //
 // Every such triangle sigma is a column whose boundary -- initially the three
-// edges of sigma -- lives in a binary max-heap of edges keyed by their
+// edges of sigma -- lives in an 8-ary max-heap of edges keyed by their
 // lexicographic key (orders of the two vertices, higher first; Sec. 2.1) in
-// a pool of device memory.  Z2 arithmetic is lazy: an edge added twice sits
+// a pool of device memory (a bump allocator: a heap that outgrows its
+// segment moves to one twice its size).  Z2 arithmetic is lazy: an edge added twice sits
 // twice in the heap and the copies cancel when they reach the top; a heap
 // about to outgrow its segment is first compacted (sorted in place, pairs
 // cancelled).  All columns work at once, in rounds of two kernels:

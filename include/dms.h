@@ -144,7 +144,9 @@ int dms_order(const float* f, dms_dims d, uint32_t* order, void* ws, size_t ws_b
  * When nx is a multiple of 4 and order is 16-byte aligned, the kernel stages
  * the order field through TMA (cp.async.bulk.tensor tile loads of one slab
  * window each, two slabs ahead); otherwise through ordinary loads.  The
- * results are the same.
+ * results are the same.  The launch tiles y by 24 rows in the grid's second
+ * dimension, so ny is at most 24 * 65535 = 1,572,840; a taller grid fails
+ * to launch and returns DMS_ERR_CUDA (the batch call has no such limit).
  */
 int dms_gradient(const uint32_t* order, dms_dims d, uint8_t* desc, uint64_t* rec,
                  int64_t* crit_counts, void* stream);
@@ -363,7 +365,9 @@ int dms_backward(const dms_pair* pairs, int64_t n, const float* g, dms_dims d, f
  * type s % 3.
  *
  * dms2_order -- as dms_order (Sec. 2.1), on nx*ny vertices.
- * dms2_gradient -- ProcessLowerStars on every vertex (Sec. 2.3):
+ * dms2_gradient -- ProcessLowerStars on every vertex (Sec. 2.3); y is tiled
+ *   by 16 rows in the launch's second dimension, so ny is at most
+ *   16 * 65535 = 1,048,560 (a taller grid returns DMS_ERR_CUDA):
  *   desc  [n] uint8 out: 0..5 the slot of the edge v is paired with, 15 a minimum.
  *   rec   [n] uint16 out, per anchor a: bits 3k..3k+2 edge k (0 = absent or
  *         paired with its top vertex, 1..2 = paired with the (code-1)-th

@@ -54,6 +54,14 @@ def _require_cuda(t: torch.Tensor, name: str, dtype=None):
         raise ValueError(f"{name} must be contiguous")
 
 
+def _require_gradient(g, rec_dtype):
+    """A gradient's arrays: on the device, contiguous, of one shape."""
+    _require_cuda(g.desc, "gradient desc", torch.uint8)
+    _require_cuda(g.rec, "gradient rec", rec_dtype)
+    if g.rec.shape != g.desc.shape or g.rec.device != g.desc.device:
+        raise ValueError("gradient rec and desc must have the same shape and device")
+
+
 def _stream(device) -> int:
     return torch.cuda.current_stream(device).cuda_stream
 
@@ -120,6 +128,7 @@ def gradient(order_t: torch.Tensor) -> Gradient:
 def critical(g: Gradient, caps=None, status: torch.Tensor | None = None):
     """Critical simplices per dimension, each list sorted by id (int64).
     Without ``caps`` the capacities are read from ``g.counts`` (one sync)."""
+    _require_gradient(g, torch.int64)
     lib = _lib.load()
     dev = g.desc.device
     d = dims_of(g.desc)
@@ -359,10 +368,19 @@ def pair_values(pairs: torch.Tensor) -> torch.Tensor:
 
 def backward(pairs: torch.Tensor, g: torch.Tensor, grad: torch.Tensor,
              status: torch.Tensor | None = None):
-    """grad[carrier] += dL/d(value) for every pair (dms_backward)."""
+    """grad[carrier] += dL/d(value) for every pair (dms_backward): pairs
+    [n, 32] pair records, g [n, 2] (dL/dbirth, dL/ddeath), grad the field's
+    gradient (float32), all on the device."""
+    _require_cuda(pairs, "pairs", torch.uint8)
+    _require_cuda(grad, "grad", torch.float32)
+    if pairs.dim() != 2 or pairs.shape[1] != PAIR_BYTES:
+        raise ValueError(f"pairs must be [n, {PAIR_BYTES}] pair records")
     lib = _lib.load()
     g = g.to(torch.float32).contiguous()
-    n = int(pairs.shape[0]) if pairs.numel() else 0
+    _require_cuda(g, "g", torch.float32)
+    n = int(pairs.shape[0])
+    if g.numel() != 2 * n:
+        raise ValueError("g must hold (dL/dbirth, dL/ddeath) for every pair")
     if n == 0:
         return grad
     st = status if status is not None else torch.zeros(1, dtype=torch.int32, device=grad.device)
@@ -457,6 +475,7 @@ def gradient2d(order_t: torch.Tensor) -> Gradient2d:
 def critical2d(g: Gradient2d, caps=None):
     """Critical vertices, edges and triangles of a 2D gradient, sorted by id.
     Without caps, a first call sizes the lists (one sync)."""
+    _require_gradient(g, torch.int16)
     lib = _lib.load()
     dev = g.desc.device
     nx, ny = dims2_of(g.desc)

@@ -2,8 +2,6 @@
 tensors before anything runs, wrong dtypes and shapes are refused before a
 kernel could index past a buffer, and a missing CUDA library is an error,
 not a fallback.  Runs without a GPU."""
-import os
-
 import numpy as np
 import pytest
 
